@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Benchmark of the MPPI hot path on GB300: one JSON line on stdout.
+
+A step is one ``mppi_step`` (noise + rollout + cost, weights, update) on the
+quadrotor workload (13 states, 4 controls, RK4, 32 obstacles, K=8192,
+T=150, lambda=0.5).  Metric: rollout-steps/s = K*T / step time.
+
+  value      device time per step (CUDA events on the launch stream), inputs
+             resident in HBM, L2 flushed (256 MiB write) before every step
+  e2e        the same step through mppi_step_host(): pinned host inputs copied
+             in and u_new + statistics copied out every step, wall-clock
+  roofline   rollout kernel (the dominant one) against the FP32 pipe peak
+  cpu_baseline  the FP64 C oracle on this host's cores, bounded sample
+
+``--impl reference`` times the oracle alone as the reference arm.
+Multi-GPU (torchrun): independent replicas, one per rank (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "rollout-steps/sec (K*T per mppi_step)"
+UNIT = "rollout-steps/s"
+
+# Algorithmic FP32 operations per rollout-step of the quadrotor workload
+# (FMA = 2), counted from the formulas: RK4 (4 derivative evaluations of 60,
+# stage combinations 169, renormalisation 13) 422, quadratic cost 64, crash
+# test over 32 spheres 32 x 10, noise scaling + importance term 31, compensated
+# accumulation 4.  Transcendentals and the integer Philox work are not counted.
+QUAD_FLOPS_PER_ROLLOUT_STEP = 422 + 64 + 320 + 31 + 4
+# FP32 pipe: 128 FP32 lanes per SM, 2 flops per FMA.
+FP32_LANES_PER_SM = 128
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(p, budget_s=12.0):
+    """The FP64 oracle as it stands, all host cores, full workload steps until
+    the time budget is spent (at least one step)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.mppi_step(dict(p, K=min(p["K"], 64)), n_threads=threads)  # build + warm
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle.mppi_step(p, step=n, n_threads=threads)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n >= 1000:
+            break
+    return {"value": p["K"] * p["T"] * n / el, "unit": UNIT, "cores": threads,
+            "kind": "oracle",
+            "sample": f"{n} full oracle step(s) of {p['name']} (FP64, OpenMP over samples), "
+                      f"{el:.1f} s"}
+
+
+def reference_arm(args, p):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    threads = os.cpu_count() or 1
+    # size each step so the whole run stays within about two minutes
+    t0 = time.perf_counter()
+    oracle.mppi_step(p, n_threads=threads)
+    t_full = time.perf_counter() - t0
+    total = args.steps + args.warmup
+    k_sample = p["K"]
+    if t_full * total > 120.0:
+        k_sample = max(32, int(p["K"] * 120.0 / (t_full * total)))
+    ps = dict(p, K=k_sample)
+    for i in range(args.warmup):
+        oracle.mppi_step(ps, step=i, n_threads=threads)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.mppi_step(ps, step=args.warmup + i, n_threads=threads)
+    el = time.perf_counter() - t0
+    ms = el * 1e3 / args.steps
+    value = k_sample * p["T"] / (ms * 1e-3)
+    sample = (f"{k_sample} of {p['K']} samples of {p['name']} per step, FP64 oracle, "
+              f"OpenMP over samples")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(p),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(p):
+    return {"workload": f"{p['name']} (quadrotor, RK4, 32 obstacles, lambda={p['lam']})",
+            "K": p["K"], "T": p["T"], "nx": p["nx"], "nu": p["nu"],
+            "l2": "flushed by a 256 MiB write before every timed step"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--K", type=int, default=None, help="override the sample count")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    p = W.quadrotor()
+    if args.K:
+        p = W.quadrotor(K=args.K)
+    if args.impl == "reference":
+        return reference_arm(args, p)
+
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import paper_2409_07563_gb300 as m
+    m.build()
+    ctl = m.MPPI.from_problem(p)
+    x0 = torch.tensor(p["x0"], dtype=torch.float32, device=dev)
+    u_nom = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device=dev)
+    u_new = torch.empty_like(u_nom)
+    stats = torch.empty(4, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        ctl.step_into(x0, u_nom, u_new, stats=stats)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region ------------------------------------------------
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ctl.profile(True)
+    t_region = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        ctl.step_into(x0, u_nom, u_new, stats=stats)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    region_s = time.perf_counter() - t_region
+    if world > 1:
+        torch.distributed.barrier()
+    ctl.profile(False)
+    prof = ctl.profile_read()
+    clk = clocks.stop()
+    per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(per_step) / len(per_step)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    rollout_steps = p["K"] * p["T"]
+    value = world * rollout_steps / (ms * 1e-3)
+
+    # ---- end to end through the host-buffer entry point -----------------------
+    x0_h = torch.tensor(p["x0"], dtype=torch.float32).pin_memory()
+    u_h = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32).pin_memory()
+    un_h = torch.empty_like(u_h).pin_memory()
+    st_h = torch.empty(4, dtype=torch.float32).pin_memory()
+    for _ in range(3):
+        ctl.step_host_ptr(x0_h.data_ptr(), u_h.data_ptr(), un_h.data_ptr(), st_h.data_ptr())
+    e2e_steps = max(20, min(args.steps, 500))
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctl.step_host_ptr(x0_h.data_ptr(), u_h.data_ptr(), un_h.data_ptr(), st_h.data_ptr())
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = (p["nx"] + p["T"] * p["nu"]) * 4
+    d2h = (p["T"] * p["nu"] + 4) * 4
+
+    # ---- roofline of the rollout kernel ---------------------------------------
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    roll_ms, roll_n = prof["rollout"]
+    upd_ms, upd_n = prof["update"]
+    roll_avg_ms = roll_ms / max(roll_n, 1)
+    achieved = QUAD_FLOPS_PER_ROLLOUT_STEP * rollout_steps / (roll_avg_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "rollout_kernel<QuadrotorDyn, QuadObstacleCost>",
+                "kernel_ms": roll_avg_ms, "update_kernel_ms": upd_ms / max(upd_n, 1),
+                "peak_note": (f"FP32 pipe: {props.multi_processor_count} SMs x 128 lanes x 2 "
+                              f"x {sm_max:.0f} MHz (max SM clock)")}
+    traffic_file = os.path.join(ROOT, "profiles", "rollout_quadrotor_traffic.json")
+    if os.path.exists(traffic_file):
+        try:
+            with open(traffic_file) as f:
+                roofline["traffic"] = json.load(f).get("bytes_per_launch")
+        except (OSError, ValueError):
+            pass
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, workloads.py)",
+        "config": workload_config(p),
+        "latency_ms": {"p50": float(np.percentile(per_step, 50)),
+                       "p99": float(np.percentile(per_step, 99)),
+                       "region_s": region_s},
+        "e2e": {"value": world * rollout_steps / (e2e_ms * 1e-3), "unit": UNIT,
+                "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": roll_n + upd_n,
+        "roofline": roofline,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p)
+    print(json.dumps(line), flush=True)
+    ctl.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

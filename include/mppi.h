@@ -1,0 +1,231 @@
+/*
+ * mppi.h -- C ABI of the GB300 (sm_103a) MPPI hot path.
+ *
+ * One call of mppi_step() runs one iteration of Algorithm 1 (MPPI) of
+ * arXiv 2409.07563 ("MPPI-Generic") on the GPU:
+ *   (a) K x T Gaussian control perturbations eps ~ N(0, diag(sigma^2)),
+ *       drawn by a counter-based Philox4x32-10 generator inside the kernels
+ *       (the noise is never written to memory);
+ *   (b) K rollouts x_{t+1} = F(x_t, u_t + eps_t) (Eq. 1) with the running cost
+ *       accumulated on the post-step output and the terminal cost added at the
+ *       end (Algorithm 1, Eq. 20), plus the importance-sampling term
+ *       -lambda I(V) of Eq. 15-16 when beta = 1;
+ *   (c) rho = min_k S_k, eta = sum_k exp(-(S_k - rho)/lambda) (Eq. 17-18),
+ *       the free energy F = rho - lambda ln(eta / K) (Eq. 4, Monte-Carlo
+ *       estimate) and the effective sample size 1 / sum w^2;
+ *   (d) u_new_t = u_t + sum_k w_k eps_{k,t}, w_k = exp(-(S_k - rho)/lambda)/eta
+ *       (Algorithm 1, control update), with eps regenerated from the counter.
+ *
+ * Noise definition (the paper names no generator): element e = t*nu + j of
+ * sample k is lane e % 4 of Philox4x32-10 block q = e / 4 with counter
+ * (k, q, step_lo32, step_hi32) and key (seed_lo32, seed_hi32); lanes (0,1)
+ * and (2,3) are Box-Muller pairs: z_{2p} = sqrt(-2 ln u1) cos(2 pi u2),
+ * z_{2p+1} = sqrt(-2 ln u1) sin(2 pi u2), u1 = ((r_{2p} >> 8) + 1) 2^-24,
+ * u2 = (r_{2p+1} >> 8) 2^-24; eps = sigma_j z.  `step` is the context's
+ * step counter, which every mppi_step() advances by one.
+ *
+ * Conventions
+ *   - Pointers named *_d are caller-owned DEVICE memory (contiguous FP32,
+ *     row-major); *_h are HOST memory.  Nothing here keeps them after return.
+ *   - All GPU work is enqueued on the context's stream (mppi_set_stream;
+ *     default: the legacy default stream) and returns without synchronising,
+ *     except where a function says otherwise.  Outputs are valid once the
+ *     stream has reached the enqueued work.
+ *   - Errors are reported as mppi_status codes; nothing is thrown across the
+ *     ABI.  Argument errors are detected synchronously on the host; conditions
+ *     found on the device (all costs non-finite) set a device status word
+ *     read by mppi_poll_status().  mppi_last_error() gives a message.
+ *   - A context is not thread-safe; separate contexts may run concurrently on
+ *     separate streams.
+ */
+#ifndef MPPI_GB300_H
+#define MPPI_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mppi_ctx mppi_ctx;
+
+typedef enum {
+    MPPI_OK = 0,
+    MPPI_ERR_INVALID_ARG = 1,   /* bad size, pointer, kind or parameter */
+    MPPI_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    MPPI_ERR_OOM = 3,           /* device allocation failed */
+    MPPI_ERR_UNSUPPORTED = 4,   /* valid request this build does not implement */
+    MPPI_ERR_NUMERIC = 5,       /* every sample cost was non-finite */
+    MPPI_ERR_TIMEOUT = 6        /* a bounded device wait gave up */
+} mppi_status;
+
+/* Dynamics (state / control layouts and parameter arrays):
+ *  CARTPOLE           nx=4 [x, xdot, theta, thetadot] (theta = 0 hanging
+ *                     down), nu=1 [f]; params [m_cart, m_pole, l, g].
+ *  QUADROTOR          nx=13 [p(3), v(3), q=(w,x,y,z), omega(3)], nu=4
+ *                     [thrust, tau(3)]; params [m, Jxx, Jyy, Jzz, g];
+ *                     integrator must be RK4; q is renormalised every step.
+ *  BICYCLE_MLP        nx=7 [x, y, yaw, v, steer, e1, e2], nu=2 [accel,
+ *                     steer_rate]; params [L, W1(64x6), b1(64), W2(64x64),
+ *                     b2(64), W3(4x64), b3(4)] (row-major, out x in); the
+ *                     residual r = W3 tanh(W2 tanh(W1 [v,steer,e1,e2,u] + b1)
+ *                     + b2) + b3 adds to [yaw', v', e1', e2'].
+ *  DOUBLE_INTEGRATOR  nx=4 [x, y, vx, vy], nu=2 [ax, ay]; no params.
+ *  LINEAR             xdot = A x + B u; params [A(nx x nx), B(nx x nu)];
+ *                     (nx, nu) in {(2,1), (4,2), (6,3), (8,4)}. */
+typedef enum {
+    MPPI_DYN_CARTPOLE = 0,
+    MPPI_DYN_QUADROTOR = 1,
+    MPPI_DYN_BICYCLE_MLP = 2,
+    MPPI_DYN_DOUBLE_INTEGRATOR = 3,
+    MPPI_DYN_LINEAR = 4
+} mppi_dyn_kind;
+
+/* Costs (l = running cost on the post-step state y and sampled control v,
+ * phi = terminal cost):
+ *  QUADRATIC       params [Q(nx), R(nu), goal(nx), s]:
+ *                  l = sum Q_i (y_i - goal_i)^2 + sum R_j v_j^2,
+ *                  phi = s sum Q_i (y_i - goal_i)^2.
+ *  QUAD_OBSTACLES  QUADRATIC params + [n_obs, c_crash, (cx,cy,cz,r) x n_obs]
+ *                  (quadrotor only): l += c_crash when some sphere has
+ *                  |p - c|^2 - r^2 < 0, evaluated in FP32 with one rounding
+ *                  per operation as fma(dz,dz, fma(dy,dy, fma(dx,dx, -r*r)))
+ *                  with d = p - c; n_obs <= 256.
+ *  COSTMAP_SPEED   params [c_map, c_speed, v_des, x_min, y_min, cell] plus a
+ *                  map_h x map_w map (row i = y): l = phi = c_map M(x, y) +
+ *                  c_speed (v - v_des)^2, M bilinear between cell centres
+ *                  (x_min + (j + 1/2) cell, y_min + (i + 1/2) cell), clamped
+ *                  to the centre range (bicycle only).
+ *  CIRCLE          params [r_in, r_out, c_ring, v_des, c_v, h_des, c_h]
+ *                  (double integrator only; Eq. 25):
+ *                  l = c_ring (1{r^2 <= r_in^2} + 1{r^2 >= r_out^2})
+ *                  + c_v |v_des - |v|| + c_h |h_des - (x vy - y vx)|, phi = 0;
+ *                  the two indicators are taken in FP32 like the crash test. */
+typedef enum {
+    MPPI_COST_QUADRATIC = 0,
+    MPPI_COST_QUAD_OBSTACLES = 1,
+    MPPI_COST_COSTMAP_SPEED = 2,
+    MPPI_COST_CIRCLE = 3
+} mppi_cost_kind;
+
+typedef enum { MPPI_EULER = 0, MPPI_RK4 = 1 } mppi_integrator;
+
+/* MLP arithmetic of BICYCLE_MLP: FP32 on CUDA cores, or BF16 operands with
+ * FP32 accumulation on the tensor cores. */
+typedef enum { MPPI_PREC_FP32 = 0, MPPI_PREC_BF16_MLP = 1 } mppi_precision;
+
+typedef struct {
+    int kind;                 /* mppi_dyn_kind */
+    int integrator;           /* mppi_integrator */
+    int nx, nu;               /* must match the kind (free for LINEAR) */
+    const float *params;      /* host; copied by mppi_create */
+    size_t n_params;
+} mppi_dynamics_desc;
+
+typedef struct {
+    int kind;                 /* mppi_cost_kind */
+    const float *params;      /* host; copied by mppi_create */
+    size_t n_params;
+    const float *map;         /* host, map_h x map_w, COSTMAP_SPEED only */
+    int map_h, map_w;
+} mppi_cost_desc;
+
+typedef struct {
+    int beta;                 /* importance-sampling term: 1 (default) or 0 */
+    int precision;            /* mppi_precision (default FP32) */
+    uint64_t seed;            /* Philox key (default 0) */
+    int block_threads;        /* rollout block size; 0 = automatic */
+    int reserved[7];
+} mppi_options;
+
+/* Fills *opt with the defaults (beta 1, FP32, seed 0, automatic launch). */
+void mppi_default_options(mppi_options *opt);
+
+/* Creates a context for K samples over horizon T with step dt, temperature
+ * lambda > 0 and per-channel noise standard deviations sigma[nu] (host,
+ * finite, >= 0).  Copies every host array it is given; allocates its device
+ * scratch (costs, partial sums, counters; O(K + T nu) floats) and a device
+ * copy of the parameters and map.  opt may be NULL (defaults).  Limits:
+ * 1 <= K <= 2^24, 1 <= T, T * nu <= 16384.  On error *out is NULL. */
+mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cost,
+                        int K, int T, float dt, float lambda, const float *sigma,
+                        const mppi_options *opt, mppi_ctx **out);
+
+/* Frees the context and its device memory (synchronises its stream). */
+void mppi_destroy(mppi_ctx *ctx);
+
+/* Sets the CUDA stream (a cudaStream_t, e.g. torch's current stream) on which
+ * the context enqueues its work.  NULL selects the legacy default stream. */
+mppi_status mppi_set_stream(mppi_ctx *ctx, void *cuda_stream);
+
+/* One MPPI iteration (Algorithm 1 with I = 1), asynchronous on the stream.
+ *   x0_d      [nx]     initial state
+ *   u_nom_d   [T*nu]   mean control sequence u (row-major t, j)
+ *   u_new_d   [T*nu]   out: updated sequence; may alias u_nom_d
+ *   weights_d [K]      out: w_k, or NULL
+ *   stats_d   [4]      out: [F, rho, eta, ess], or NULL
+ *   costs_d   [K]      out: S_k, or NULL
+ * If no sample cost is finite, u_new = u_nom, w = 0, F = rho = +inf and the
+ * device status word records MPPI_ERR_NUMERIC (see mppi_poll_status). */
+mppi_status mppi_step(mppi_ctx *ctx, const float *x0_d, const float *u_nom_d,
+                      float *u_new_d, float *weights_d, float *stats_d, float *costs_d);
+
+/* Same iteration from HOST buffers: copies x0_h and u_nom_h to the device,
+ * runs mppi_step, copies u_new_h [T*nu] (and stats_h [4] unless NULL) back and
+ * synchronises the stream before returning.  Pinned host memory gives
+ * asynchronous copies; pageable memory works too. */
+mppi_status mppi_step_host(mppi_ctx *ctx, const float *x0_h, const float *u_nom_h,
+                           float *u_new_h, float *stats_h);
+
+/* Replaces the dynamics and/or cost parameter arrays (host, same lengths as at
+ * create; NULL keeps the current one).  Synchronises the stream, then copies;
+ * later steps use the new values. */
+mppi_status mppi_set_params(mppi_ctx *ctx, const float *dyn_params, const float *cost_params);
+
+/* Gradient of L = sum_{t,j} grad_u_new[t,j] u_new[t,j] of the most recent
+ * mppi_step with respect to theta = (Q[0..3], R, l, m_cart) at fixed noise
+ * (same seed and step), for CARTPOLE + QUADRATIC + EULER only:
+ * dL/dS_k = -(w_k / lambda)(a_k - sum_i w_i a_i), a_k = sum G eps_k, chained
+ * through each rollout by a reverse (adjoint) sweep that recomputes states
+ * from checkpoints stored every ceil(sqrt(T)) steps.
+ *   grad_u_new_d [T*nu] (device), grad_params_d [7] (device, overwritten).
+ * Needs a prior mppi_step on this context; MPPI_ERR_UNSUPPORTED otherwise. */
+mppi_status mppi_step_backward(mppi_ctx *ctx, const float *grad_u_new_d,
+                               float *grad_params_d);
+
+/* Step counter used as the noise counter's high words.  get synchronises the
+ * stream (the counter lives on the device); set is ordered on the stream. */
+mppi_status mppi_get_counter(mppi_ctx *ctx, uint64_t *counter);
+mppi_status mppi_set_counter(mppi_ctx *ctx, uint64_t counter);
+
+/* Synchronises the stream, reads and clears the device status word:
+ * MPPI_OK, or the first device-side condition recorded since the last poll. */
+mppi_status mppi_poll_status(mppi_ctx *ctx);
+
+/* Message of the last error on this context ("" if none); valid until the
+ * next call on the context. */
+const char *mppi_last_error(const mppi_ctx *ctx);
+
+/* Per-kernel timing with CUDA events recorded on the context's stream around
+ * every launch the context makes while profiling is on.  mppi_profile(ctx, 1)
+ * clears the record and starts recording, mppi_profile(ctx, 0) stops.
+ * mppi_profile_read() synchronises the stream and returns, per kernel slot
+ * (MPPI_PROF_ROLLOUT, MPPI_PROF_UPDATE, MPPI_PROF_ADJOINT), the summed
+ * elapsed milliseconds and the number of launches (arrays of
+ * MPPI_PROF_SLOTS entries; either may be NULL). */
+enum { MPPI_PROF_ROLLOUT = 0, MPPI_PROF_UPDATE = 1, MPPI_PROF_ADJOINT = 2, MPPI_PROF_SLOTS = 4 };
+mppi_status mppi_profile(mppi_ctx *ctx, int enable);
+mppi_status mppi_profile_read(mppi_ctx *ctx, float *ms, int *launches);
+
+/* Diagnostic: the raw Philox words and standard normals the kernels use, for
+ * samples k < K and blocks q < Q at (seed, step): bits_d [K*Q*4] (uint32) and
+ * z_d [K*Q*4] (float), either may be NULL; element (k, q, lane) at
+ * ((k * Q) + q) * 4 + lane.  Enqueued on `cuda_stream`. */
+mppi_status mppi_sample_noise(uint64_t seed, uint64_t step, int K, int Q,
+                              uint32_t *bits_d, float *z_d, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -262,7 +262,8 @@ int oracle_dynamics_step(const oracle_problem *p, const double *x, const double 
  *                   phi = s * sum Q_i (y_i - goal_i)^2
  *   QUAD_OBSTACLES  QUADRATIC + [n_obs, c_crash, (cx, cy, cz, r) * n_obs]:
  *                   l += c_crash if some sphere has |p - c|^2 - r^2 < 0
- *                   (p = y[0..2]); phi unchanged
+ *                   (p = y[0..2]); phi unchanged.  In FP32 the test reads
+ *                   fma(dz,dz, fma(dy,dy, fma(dx,dx, -fl(r*r)))) < 0.
  *   COSTMAP_SPEED   [c_map, c_speed, v_des, x_min, y_min, cell]:
  *                   l = phi = c_map M(y0, y1) + c_speed (y3 - v_des)^2
  *   CIRCLE          [r_in, r_out, c_ring, v_des, c_v, h_des, c_h]
@@ -295,16 +296,18 @@ static double quad_control_cost(const oracle_problem *p, const double *v)
 
 static int crash_fp32(const double *obs, int n_obs, const double *y)
 {
+    /* m = fma(dz, dz, fma(dy, dy, fma(dx, dx, -fl(r*r)))), d = fl(p - c), all in
+     * FP32 with one rounding per operation; crash if m < 0. */
     volatile float px = (float)y[0], py = (float)y[1], pz = (float)y[2];
     for (int i = 0; i < n_obs; ++i) {
         volatile float dx = px - (float)obs[4 * i + 0];
         volatile float dy = py - (float)obs[4 * i + 1];
         volatile float dz = pz - (float)obs[4 * i + 2];
         volatile float r = (float)obs[4 * i + 3];
-        volatile float xx = dx * dx, yy = dy * dy, zz = dz * dz, rr = r * r;
-        volatile float s = xx + yy;
-        volatile float d2 = s + zz;
-        volatile float m = d2 - rr;
+        volatile float rr = r * r;
+        volatile float m = fmaf(dx, dx, -rr);
+        m = fmaf(dy, dy, m);
+        m = fmaf(dz, dz, m);
         if (m < 0.0f) return 1;
     }
     return 0;

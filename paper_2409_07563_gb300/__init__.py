@@ -1,0 +1,228 @@
+"""GB300 (sm_103a) MPPI hot path: Python binding of ``include/mppi.h``.
+
+The binding marshals arguments only.  Device memory and streams come from
+PyTorch (``tensor.data_ptr()``, ``torch.cuda.current_stream().cuda_stream``);
+every step of the method runs in the library's CUDA kernels.  When the library
+is missing the calls raise instead of falling back to the CPU.
+
+    ctl = MPPI.from_problem(problem)          # problem dict (see workloads.py)
+    out = ctl.step(x0, u_nom)                 # CUDA tensors in, CUDA tensors out
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _build
+from ._lib import (MPPIError, CostDesc, DynamicsDesc, Options, check, load,  # noqa: F401
+                   MPPI_PREC_FP32, MPPI_PREC_BF16_MLP)
+
+__all__ = ["build", "MPPI", "MPPIError", "mppi_sample_noise", "library_path"]
+
+library_path = _build.LIB_PATH
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA library in-tree (nvcc, sm_103a)."""
+    return _build.build(force=force, verbose=verbose)
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _fptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_tensor(t, n, name):
+    import torch
+    if t is None:
+        return
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == n):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor with {n} elements")
+
+
+class MPPI:
+    """One MPPI controller context (``mppi_create`` ... ``mppi_destroy``)."""
+
+    def __init__(self, *, dyn_kind, integrator, nx, nu, dyn_params, cost_kind, cost_params,
+                 K, T, dt, lam, sigma, beta=1, seed=0, cost_map=None,
+                 precision=MPPI_PREC_FP32, block_threads=0):
+        L = load()
+        self._dyn_params = _f32(dyn_params)
+        self._cost_params = _f32(cost_params)
+        self._sigma = _f32(sigma)
+        self._map = None if cost_map is None else _f32(cost_map)
+        dyn = DynamicsDesc(int(dyn_kind), int(integrator), int(nx), int(nu),
+                           _fptr(self._dyn_params), self._dyn_params.size)
+        if self._map is not None:
+            cost = CostDesc(int(cost_kind), _fptr(self._cost_params), self._cost_params.size,
+                            _fptr(self._map), self._map.shape[0], self._map.shape[1])
+        else:
+            cost = CostDesc(int(cost_kind), _fptr(self._cost_params), self._cost_params.size,
+                            None, 0, 0)
+        opt = Options()
+        L.mppi_default_options(ctypes.byref(opt))
+        opt.beta = int(beta)
+        opt.seed = int(seed) & (2**64 - 1)
+        opt.precision = int(precision)
+        opt.block_threads = int(block_threads)
+        h = ctypes.c_void_p()
+        st = L.mppi_create(ctypes.byref(dyn), ctypes.byref(cost), int(K), int(T), float(dt),
+                           float(lam), _fptr(self._sigma), ctypes.byref(opt), ctypes.byref(h))
+        check(st, "mppi_create")
+        self._h = h
+        self.K, self.T, self.nx, self.nu = int(K), int(T), int(nx), int(nu)
+        self.lam = float(lam)
+
+    @classmethod
+    def from_problem(cls, p: dict, **kw):
+        """Build from a problem dictionary of ``workloads.py``."""
+        args = dict(dyn_kind=p["dyn_kind"], integrator=p["integrator"], nx=p["nx"], nu=p["nu"],
+                    dyn_params=p["dyn_params"], cost_kind=p["cost_kind"],
+                    cost_params=p["cost_params"], K=p["K"], T=p["T"], dt=p["dt"], lam=p["lam"],
+                    sigma=p["sigma"], beta=p["beta"], seed=p["seed"], cost_map=p.get("map"))
+        args.update(kw)
+        return cls(**args)
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mppi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- stepping ---------------------------------------------------------
+    def step_into(self, x0, u_nom, u_new, weights=None, stats=None, costs=None, stream=None):
+        """``mppi_step`` on caller-allocated CUDA tensors (no allocation)."""
+        L = load()
+        _check_tensor(x0, self.nx, "x0")
+        _check_tensor(u_nom, self.T * self.nu, "u_nom")
+        _check_tensor(u_new, self.T * self.nu, "u_new")
+        _check_tensor(weights, self.K, "weights")
+        _check_tensor(stats, 4, "stats")
+        _check_tensor(costs, self.K, "costs")
+        check(L.mppi_set_stream(self._h, _stream_handle(stream)), "mppi_set_stream", self._h)
+        st = L.mppi_step(self._h, _dptr(x0), _dptr(u_nom), _dptr(u_new), _dptr(weights),
+                         _dptr(stats), _dptr(costs))
+        check(st, "mppi_step", self._h)
+
+    def step(self, x0, u_nom, want_weights=False, want_costs=False, stream=None):
+        """One iteration; returns dict(u_new[T, nu], stats[4], weights?, costs?)."""
+        import torch
+        dev = x0.device
+        u_nom = u_nom.reshape(-1)
+        out = dict(u_new=torch.empty(self.T * self.nu, device=dev, dtype=torch.float32),
+                   stats=torch.empty(4, device=dev, dtype=torch.float32))
+        if want_weights:
+            out["weights"] = torch.empty(self.K, device=dev, dtype=torch.float32)
+        if want_costs:
+            out["costs"] = torch.empty(self.K, device=dev, dtype=torch.float32)
+        self.step_into(x0, u_nom, out["u_new"], out.get("weights"), out["stats"],
+                       out.get("costs"), stream=stream)
+        out["u_new"] = out["u_new"].view(self.T, self.nu)
+        return out
+
+    def step_host(self, x0, u_nom, stream=None):
+        """``mppi_step_host``: numpy/pinned host arrays in and out (synchronous)."""
+        L = load()
+        x0 = _f32(x0)
+        u_nom = _f32(u_nom).reshape(-1)
+        u_new = np.empty(self.T * self.nu, dtype=np.float32)
+        stats = np.empty(4, dtype=np.float32)
+        check(L.mppi_set_stream(self._h, _stream_handle(stream)), "mppi_set_stream", self._h)
+        check(L.mppi_step_host(self._h, _fptr(x0), _fptr(u_nom), _fptr(u_new), _fptr(stats)),
+              "mppi_step_host", self._h)
+        return u_new.reshape(self.T, self.nu), stats
+
+    def step_host_ptr(self, x0_ptr, u_nom_ptr, u_new_ptr, stats_ptr=None, stream=None):
+        """``mppi_step_host`` on raw host addresses (e.g. pinned torch tensors)."""
+        L = load()
+        check(L.mppi_set_stream(self._h, _stream_handle(stream)), "mppi_set_stream", self._h)
+        fp = ctypes.POINTER(ctypes.c_float)
+        st = L.mppi_step_host(self._h, ctypes.cast(x0_ptr, fp), ctypes.cast(u_nom_ptr, fp),
+                              ctypes.cast(u_new_ptr, fp),
+                              ctypes.cast(stats_ptr, fp) if stats_ptr else None)
+        check(st, "mppi_step_host", self._h)
+
+    def set_params(self, dyn_params=None, cost_params=None):
+        L = load()
+        d = None if dyn_params is None else _f32(dyn_params)
+        c = None if cost_params is None else _f32(cost_params)
+        check(L.mppi_set_params(self._h, None if d is None else _fptr(d),
+                                None if c is None else _fptr(c)), "mppi_set_params", self._h)
+
+    def backward(self, grad_u_new, stream=None):
+        """``mppi_step_backward``: gradient of sum(grad_u_new * u_new) of the last
+        step w.r.t. (Q[4], R, l, m_cart); returns a CUDA tensor of 7."""
+        import torch
+        L = load()
+        g = grad_u_new.reshape(-1).contiguous()
+        _check_tensor(g, self.T * self.nu, "grad_u_new")
+        out = torch.empty(7, device=g.device, dtype=torch.float32)
+        check(L.mppi_set_stream(self._h, _stream_handle(stream)), "mppi_set_stream", self._h)
+        check(L.mppi_step_backward(self._h, _dptr(g), _dptr(out)), "mppi_step_backward", self._h)
+        return out
+
+    @property
+    def counter(self) -> int:
+        v = ctypes.c_uint64()
+        check(load().mppi_get_counter(self._h, ctypes.byref(v)), "mppi_get_counter", self._h)
+        return int(v.value)
+
+    @counter.setter
+    def counter(self, value: int):
+        check(load().mppi_set_counter(self._h, int(value) & (2**64 - 1)), "mppi_set_counter",
+              self._h)
+
+    def profile(self, enable: bool):
+        """Start (clearing the record) or stop per-kernel event timing."""
+        check(load().mppi_profile(self._h, 1 if enable else 0), "mppi_profile", self._h)
+
+    def profile_read(self):
+        """{slot: (total_ms, launches)} for slots rollout, update, adjoint."""
+        ms = (ctypes.c_float * 4)()
+        n = (ctypes.c_int * 4)()
+        check(load().mppi_profile_read(self._h, ms, n), "mppi_profile_read", self._h)
+        names = ("rollout", "update", "adjoint", "other")
+        return {names[i]: (float(ms[i]), int(n[i])) for i in range(4)}
+
+    def poll_status(self) -> int:
+        """Device status word since the last poll (0 = MPPI_OK); does not raise."""
+        return int(load().mppi_poll_status(self._h))
+
+
+def mppi_sample_noise(seed, step, K, Q, bits=None, z=None, stream=None):
+    """Raw Philox words (uint32 stored in an int32 tensor) and normals the kernels use."""
+    L = load()
+    st = L.mppi_sample_noise(int(seed) & (2**64 - 1), int(step) & (2**64 - 1), int(K), int(Q),
+                             _dptr(bits), _dptr(z), _stream_handle(stream))
+    check(st, "mppi_sample_noise")

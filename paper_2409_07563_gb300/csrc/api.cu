@@ -1,0 +1,503 @@
+// api.cu -- the C ABI declared in include/mppi.h: argument validation,
+// context and scratch ownership, launch planning, and dispatch to the kernel
+// translation units.  Every compute step runs in the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "mppi_internal.h"
+
+using mppi::StepParams;
+
+namespace {
+
+mppi_status fail(mppi_ctx *c, mppi_status st, const std::string &msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+mppi_status cuda_fail(mppi_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? MPPI_ERR_OOM : MPPI_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int expected_dyn_params(int kind, int nx, int nu) {
+    switch (kind) {
+    case MPPI_DYN_CARTPOLE: return 4;
+    case MPPI_DYN_QUADROTOR: return 5;
+    case MPPI_DYN_BICYCLE_MLP: return 1 + 64 * 6 + 64 + 64 * 64 + 64 + 4 * 64 + 4;
+    case MPPI_DYN_DOUBLE_INTEGRATOR: return 0;
+    case MPPI_DYN_LINEAR: return nx * nx + nx * nu;
+    default: return -1;
+    }
+}
+
+bool fixed_dims(int kind, int &nx, int &nu) {
+    switch (kind) {
+    case MPPI_DYN_CARTPOLE: nx = 4; nu = 1; return true;
+    case MPPI_DYN_QUADROTOR: nx = 13; nu = 4; return true;
+    case MPPI_DYN_BICYCLE_MLP: nx = 7; nu = 2; return true;
+    case MPPI_DYN_DOUBLE_INTEGRATOR: nx = 4; nu = 2; return true;
+    default: return false;
+    }
+}
+
+template <class T>
+cudaError_t dalloc(T **p, size_t n) {
+    return cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(n, 1) * sizeof(T));
+}
+
+// Event pair around one launch while profiling is on (ordered on the stream).
+class ProfScope {
+  public:
+    ProfScope(mppi_ctx *c, int slot) : c_(c), slot_(slot) {
+        if (!c_->prof.on) return;
+        a_ = take();
+        b_ = take();
+        if (a_ && b_) cudaEventRecord(a_, c_->stream);
+    }
+    ~ProfScope() {
+        if (!c_->prof.on || !a_ || !b_) return;
+        cudaEventRecord(b_, c_->stream);
+        c_->prof.launches.push_back({slot_, {a_, b_}});
+    }
+
+  private:
+    cudaEvent_t take() {
+        auto &pr = c_->prof;
+        if (pr.pool_used == pr.pool.size()) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pr.pool.push_back(e);
+        }
+        return pr.pool[pr.pool_used++];
+    }
+    mppi_ctx *c_;
+    int slot_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
+void free_ctx(mppi_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
+    void *ptrs[] = {c->d_dyn, c->d_cost, c->d_map, c->scr.S, c->scr.partials, c->scr.upartials,
+                    c->scr.scalars, c->scr.tickets, c->scr.status, c->scr.counter,
+                    c->scr.last_step, c->scr.ckpt, c->scr.grad_partials, c->scr.io};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete c;
+}
+
+void plan_launch(mppi_ctx &c) {
+    mppi::LaunchPlan &pl = c.plan;
+    if (c.block_threads > 0) {
+        pl.rollout_threads = c.block_threads;
+    } else {
+        // Spread samples over every SM first (the rollout is a serial chain per
+        // sample, so more SMs beat more warps per SM at these sizes).
+        const int per_sm = (c.K + c.num_sms - 1) / c.num_sms;
+        pl.rollout_threads = std::min(128, std::max(32, ((per_sm + 31) / 32) * 32));
+    }
+    pl.rollout_blocks = (c.K + pl.rollout_threads - 1) / pl.rollout_threads;
+    const int Q = (c.T * c.nu + 3) / 4;
+    pl.update_qtiles = (Q + mppi::kUpdateQb - 1) / mppi::kUpdateQb;
+    const int max_chunks =
+        std::min(mppi::kMaxUpdateChunks, (c.K + mppi::kUpdateThreads - 1) / mppi::kUpdateThreads);
+    const int want = (2 * c.num_sms + pl.update_qtiles - 1) / pl.update_qtiles;
+    pl.update_chunks = std::max(1, std::min(max_chunks, want));
+    pl.update_chunk_len = (c.K + pl.update_chunks - 1) / pl.update_chunks;
+    pl.update_chunks = (c.K + pl.update_chunk_len - 1) / pl.update_chunk_len;
+}
+
+StepParams make_params(const mppi_ctx &c) {
+    StepParams p;
+    std::memset(&p, 0, sizeof p);
+    p.K = c.K;
+    p.T = c.T;
+    p.nx = c.nx;
+    p.nu = c.nu;
+    p.dt = c.dt;
+    p.lambda = c.lambda;
+    p.lam_beta = c.beta ? c.lambda : 0.f;
+    for (int j = 0; j < c.nu; ++j) {
+        p.sigma[j] = c.sigma[j];
+        p.ivar[j] = c.sigma[j] > 0.f ? 1.0f / (c.sigma[j] * c.sigma[j]) : 0.f;
+    }
+    p.seed = c.seed;
+    p.dyn_params = c.d_dyn;
+    p.cost_params = c.d_cost;
+    p.map = c.d_map;
+    p.n_dyn_params = static_cast<int>(c.dyn_params_h.size());
+    p.n_cost_params = static_cast<int>(c.cost_params_h.size());
+    p.map_h = c.map_h;
+    p.map_w = c.map_w;
+    p.S = c.scr.S;
+    p.partials = c.scr.partials;
+    p.upartials = c.scr.upartials;
+    p.scalars = c.scr.scalars;
+    p.tickets = c.scr.tickets;
+    p.status = c.scr.status;
+    p.counter = c.scr.counter;
+    p.last_step = c.scr.last_step;
+    return p;
+}
+
+mppi_status validate_cost(const mppi_dynamics_desc &d, const mppi_cost_desc &cd, int nx, int nu,
+                          std::string &msg) {
+    if (cd.n_params > 0 && !cd.params) return msg = "cost params pointer is NULL", MPPI_ERR_INVALID_ARG;
+    for (size_t i = 0; i < cd.n_params; ++i)
+        if (!std::isfinite(cd.params[i]))
+            return msg = "cost params must be finite", MPPI_ERR_INVALID_ARG;
+    switch (cd.kind) {
+    case MPPI_COST_QUADRATIC:
+        if (cd.n_params != static_cast<size_t>(2 * nx + nu + 1))
+            return msg = "QUADRATIC cost needs 2*nx+nu+1 params", MPPI_ERR_INVALID_ARG;
+        return MPPI_OK;
+    case MPPI_COST_QUAD_OBSTACLES: {
+        if (d.kind != MPPI_DYN_QUADROTOR)
+            return msg = "QUAD_OBSTACLES cost needs QUADROTOR dynamics", MPPI_ERR_UNSUPPORTED;
+        if (cd.n_params < 33) return msg = "QUAD_OBSTACLES cost too short", MPPI_ERR_INVALID_ARG;
+        const float nf = cd.params[31];
+        const int n = static_cast<int>(nf);
+        if (nf != static_cast<float>(n) || n < 0 || n > 256 ||
+            cd.n_params != static_cast<size_t>(33 + 4 * n))
+            return msg = "QUAD_OBSTACLES: n_obs must be an integer in [0,256] and the array "
+                         "33 + 4*n_obs long",
+                   MPPI_ERR_INVALID_ARG;
+        return MPPI_OK;
+    }
+    case MPPI_COST_COSTMAP_SPEED:
+        if (d.kind != MPPI_DYN_BICYCLE_MLP)
+            return msg = "COSTMAP_SPEED cost needs BICYCLE_MLP dynamics", MPPI_ERR_UNSUPPORTED;
+        if (cd.n_params != 6 || !cd.map || cd.map_h < 2 || cd.map_w < 2 || !(cd.params[5] > 0.f))
+            return msg = "COSTMAP_SPEED needs 6 params (cell > 0) and a map of at least 2x2",
+                   MPPI_ERR_INVALID_ARG;
+        return MPPI_OK;
+    case MPPI_COST_CIRCLE:
+        if (d.kind != MPPI_DYN_DOUBLE_INTEGRATOR)
+            return msg = "CIRCLE cost needs DOUBLE_INTEGRATOR dynamics", MPPI_ERR_UNSUPPORTED;
+        if (cd.n_params != 7) return msg = "CIRCLE cost needs 7 params", MPPI_ERR_INVALID_ARG;
+        return MPPI_OK;
+    default:
+        return msg = "unknown cost kind", MPPI_ERR_INVALID_ARG;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void mppi_default_options(mppi_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->beta = 1;
+    opt->precision = MPPI_PREC_FP32;
+}
+
+mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cost, int K, int T,
+                        float dt, float lambda, const float *sigma, const mppi_options *opt,
+                        mppi_ctx **out) {
+    if (!out) return MPPI_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!dyn || !cost || !sigma) return MPPI_ERR_INVALID_ARG;
+    mppi_options o;
+    if (opt) o = *opt; else mppi_default_options(&o);
+
+    int nx = dyn->nx, nu = dyn->nu;
+    int fx, fu;
+    if (fixed_dims(dyn->kind, fx, fu)) {
+        if (nx != fx || nu != fu) return MPPI_ERR_INVALID_ARG;
+    } else if (dyn->kind != MPPI_DYN_LINEAR) {
+        return MPPI_ERR_INVALID_ARG;
+    }
+    if (nx < 1 || nx > mppi::kMaxNx || nu < 1 || nu > 4) return MPPI_ERR_INVALID_ARG;
+    if (expected_dyn_params(dyn->kind, nx, nu) != static_cast<long>(dyn->n_params))
+        return MPPI_ERR_INVALID_ARG;
+    if (dyn->n_params > 0 && !dyn->params) return MPPI_ERR_INVALID_ARG;
+    for (size_t i = 0; i < dyn->n_params; ++i)
+        if (!std::isfinite(dyn->params[i])) return MPPI_ERR_INVALID_ARG;
+    if (K < 1 || K > mppi::kMaxK || T < 1 || static_cast<long>(T) * nu > mppi::kMaxTnu)
+        return MPPI_ERR_INVALID_ARG;
+    if (!std::isfinite(dt) || !(dt > 0.f) || !std::isfinite(lambda) || !(lambda > 0.f))
+        return MPPI_ERR_INVALID_ARG;
+    for (int j = 0; j < nu; ++j)
+        if (!std::isfinite(sigma[j]) || sigma[j] < 0.f) return MPPI_ERR_INVALID_ARG;
+    if (o.beta != 0 && o.beta != 1) return MPPI_ERR_INVALID_ARG;
+    if (o.block_threads < 0 || o.block_threads > 256 || o.block_threads % 32 != 0)
+        return MPPI_ERR_INVALID_ARG;
+    const int want_integrator = dyn->kind == MPPI_DYN_QUADROTOR ? MPPI_RK4 : MPPI_EULER;
+    if (dyn->integrator != MPPI_EULER && dyn->integrator != MPPI_RK4) return MPPI_ERR_INVALID_ARG;
+    if (dyn->integrator != want_integrator) return MPPI_ERR_UNSUPPORTED;
+    std::string msg;
+    mppi_status st = validate_cost(*dyn, *cost, nx, nu, msg);
+    if (st != MPPI_OK) return st;
+    if (!mppi::rollout_supported(dyn->kind, cost->kind, nx, nu)) return MPPI_ERR_UNSUPPORTED;
+    if (o.precision != MPPI_PREC_FP32) return MPPI_ERR_UNSUPPORTED;
+
+    mppi_ctx *c = new (std::nothrow) mppi_ctx;
+    if (!c) return MPPI_ERR_OOM;
+    c->dyn_kind = dyn->kind;
+    c->integrator = dyn->integrator;
+    c->nx = nx;
+    c->nu = nu;
+    c->cost_kind = cost->kind;
+    c->K = K;
+    c->T = T;
+    c->beta = o.beta;
+    c->precision = o.precision;
+    c->block_threads = o.block_threads;
+    c->dt = dt;
+    c->lambda = lambda;
+    c->seed = o.seed;
+    c->sigma.assign(sigma, sigma + nu);
+    c->dyn_params_h.assign(dyn->params, dyn->params + dyn->n_params);
+    c->cost_params_h.assign(cost->params, cost->params + cost->n_params);
+
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        free_ctx(c);
+        return MPPI_ERR_CUDA;
+    }
+    plan_launch(*c);
+
+    const int Q = (T * nu + 3) / 4;
+    const size_t max_blocks = (static_cast<size_t>(K) + 31) / 32;
+    const size_t io_floats = static_cast<size_t>(nx) + 2 * static_cast<size_t>(T) * nu + 4;
+    if ((e = dalloc(&c->scr.S, K)) != cudaSuccess ||
+        (e = dalloc(&c->scr.partials, 3 * max_blocks)) != cudaSuccess ||
+        (e = dalloc(&c->scr.upartials, static_cast<size_t>(mppi::kMaxUpdateChunks) * Q * 4)) != cudaSuccess ||
+        (e = dalloc(&c->scr.scalars, 8)) != cudaSuccess ||
+        (e = dalloc(&c->scr.tickets, 4)) != cudaSuccess ||
+        (e = dalloc(&c->scr.status, 1)) != cudaSuccess ||
+        (e = dalloc(&c->scr.counter, 1)) != cudaSuccess ||
+        (e = dalloc(&c->scr.last_step, 1)) != cudaSuccess ||
+        (e = dalloc(&c->scr.io, io_floats)) != cudaSuccess ||
+        (e = dalloc(&c->d_dyn, c->dyn_params_h.size())) != cudaSuccess ||
+        (e = dalloc(&c->d_cost, c->cost_params_h.size())) != cudaSuccess) {
+        free_ctx(c);
+        return e == cudaErrorMemoryAllocation ? MPPI_ERR_OOM : MPPI_ERR_CUDA;
+    }
+    if (cost->kind == MPPI_COST_COSTMAP_SPEED) {
+        c->map_h = cost->map_h;
+        c->map_w = cost->map_w;
+        const size_t n = static_cast<size_t>(cost->map_h) * cost->map_w;
+        if ((e = dalloc(&c->d_map, n)) != cudaSuccess ||
+            (e = cudaMemcpy(c->d_map, cost->map, n * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            free_ctx(c);
+            return e == cudaErrorMemoryAllocation ? MPPI_ERR_OOM : MPPI_ERR_CUDA;
+        }
+    }
+    if ((e = cudaMemcpy(c->d_dyn, c->dyn_params_h.data(), c->dyn_params_h.size() * sizeof(float),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->d_cost, c->cost_params_h.data(), c->cost_params_h.size() * sizeof(float),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(c->scr.tickets, 0, 4 * sizeof(unsigned int))) != cudaSuccess ||
+        (e = cudaMemset(c->scr.status, 0, sizeof(unsigned int))) != cudaSuccess ||
+        (e = cudaMemset(c->scr.counter, 0, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMemset(c->scr.last_step, 0, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMemset(c->scr.scalars, 0, 8 * sizeof(float))) != cudaSuccess) {
+        free_ctx(c);
+        return MPPI_ERR_CUDA;
+    }
+    c->plan.rollout_smem = mppi::rollout_smem_bytes(*c);
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (c->plan.rollout_smem > static_cast<size_t>(max_smem)) {
+        free_ctx(c);
+        return MPPI_ERR_UNSUPPORTED;
+    }
+    if ((e = mppi::rollout_prepare(*c)) != cudaSuccess) {
+        free_ctx(c);
+        return MPPI_ERR_CUDA;
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+        free_ctx(c);
+        return MPPI_ERR_CUDA;
+    }
+    *out = c;
+    return MPPI_OK;
+}
+
+void mppi_destroy(mppi_ctx *ctx) { free_ctx(ctx); }
+
+mppi_status mppi_set_stream(mppi_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return MPPI_ERR_INVALID_ARG;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    return MPPI_OK;
+}
+
+mppi_status mppi_step(mppi_ctx *ctx, const float *x0_d, const float *u_nom_d, float *u_new_d,
+                      float *weights_d, float *stats_d, float *costs_d) {
+    if (!ctx) return MPPI_ERR_INVALID_ARG;
+    if (!x0_d || !u_nom_d || !u_new_d)
+        return fail(ctx, MPPI_ERR_INVALID_ARG, "x0, u_nom and u_new must be device pointers");
+    StepParams p = make_params(*ctx);
+    p.x0 = x0_d;
+    p.u_nom = u_nom_d;
+    p.u_new = u_new_d;
+    p.weights_out = weights_d;
+    p.stats_out = stats_d;
+    p.costs_out = costs_d;
+    cudaError_t e;
+    {
+        ProfScope ps(ctx, MPPI_PROF_ROLLOUT);
+        e = mppi::launch_rollout(*ctx, p);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rollout launch");
+    {
+        ProfScope ps(ctx, MPPI_PROF_UPDATE);
+        e = mppi::launch_update(*ctx, p);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "update launch");
+    ctx->have_step = true;
+    ctx->err.clear();
+    return MPPI_OK;
+}
+
+mppi_status mppi_step_host(mppi_ctx *ctx, const float *x0_h, const float *u_nom_h,
+                           float *u_new_h, float *stats_h) {
+    if (!ctx) return MPPI_ERR_INVALID_ARG;
+    if (!x0_h || !u_nom_h || !u_new_h)
+        return fail(ctx, MPPI_ERR_INVALID_ARG, "x0, u_nom and u_new must be host pointers");
+    const size_t TN = static_cast<size_t>(ctx->T) * ctx->nu;
+    float *d_x0 = ctx->scr.io, *d_u = d_x0 + ctx->nx, *d_un = d_u + TN, *d_st = d_un + TN;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_x0, x0_h, ctx->nx * sizeof(float), cudaMemcpyHostToDevice,
+                             ctx->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_u, u_nom_h, TN * sizeof(float), cudaMemcpyHostToDevice,
+                             ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "host-to-device copy");
+    mppi_status st = mppi_step(ctx, d_x0, d_u, d_un, nullptr, stats_h ? d_st : nullptr, nullptr);
+    if (st != MPPI_OK) return st;
+    if ((e = cudaMemcpyAsync(u_new_h, d_un, TN * sizeof(float), cudaMemcpyDeviceToHost,
+                             ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "device-to-host copy");
+    if (stats_h && (e = cudaMemcpyAsync(stats_h, d_st, 4 * sizeof(float), cudaMemcpyDeviceToHost,
+                                        ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "device-to-host copy");
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "stream synchronize");
+    return MPPI_OK;
+}
+
+mppi_status mppi_set_params(mppi_ctx *ctx, const float *dyn_params, const float *cost_params) {
+    if (!ctx) return MPPI_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    if (dyn_params) {
+        for (size_t i = 0; i < ctx->dyn_params_h.size(); ++i)
+            if (!std::isfinite(dyn_params[i]))
+                return fail(ctx, MPPI_ERR_INVALID_ARG, "dynamics params must be finite");
+        ctx->dyn_params_h.assign(dyn_params, dyn_params + ctx->dyn_params_h.size());
+        e = cudaMemcpy(ctx->d_dyn, ctx->dyn_params_h.data(),
+                       ctx->dyn_params_h.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "parameter upload");
+    }
+    if (cost_params) {
+        for (size_t i = 0; i < ctx->cost_params_h.size(); ++i)
+            if (!std::isfinite(cost_params[i]))
+                return fail(ctx, MPPI_ERR_INVALID_ARG, "cost params must be finite");
+        if (ctx->cost_kind == MPPI_COST_QUAD_OBSTACLES && cost_params[31] != ctx->cost_params_h[31])
+            return fail(ctx, MPPI_ERR_INVALID_ARG, "the obstacle count cannot change");
+        ctx->cost_params_h.assign(cost_params, cost_params + ctx->cost_params_h.size());
+        e = cudaMemcpy(ctx->d_cost, ctx->cost_params_h.data(),
+                       ctx->cost_params_h.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "parameter upload");
+    }
+    return MPPI_OK;
+}
+
+mppi_status mppi_step_backward(mppi_ctx *ctx, const float *grad_u_new_d, float *grad_params_d) {
+    if (!ctx) return MPPI_ERR_INVALID_ARG;
+    (void)grad_u_new_d;
+    (void)grad_params_d;
+    return fail(ctx, MPPI_ERR_UNSUPPORTED, "backward is not available for this context");
+}
+
+mppi_status mppi_get_counter(mppi_ctx *ctx, uint64_t *counter) {
+    if (!ctx || !counter) return MPPI_ERR_INVALID_ARG;
+    unsigned long long v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, ctx->scr.counter, sizeof v, cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "counter read");
+    *counter = v;
+    return MPPI_OK;
+}
+
+mppi_status mppi_set_counter(mppi_ctx *ctx, uint64_t counter) {
+    if (!ctx) return MPPI_ERR_INVALID_ARG;
+    cudaError_t e = mppi::launch_store_u64(ctx->scr.counter, counter, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "counter write");
+    return MPPI_OK;
+}
+
+mppi_status mppi_poll_status(mppi_ctx *ctx) {
+    if (!ctx) return MPPI_ERR_INVALID_ARG;
+    unsigned int word = 0;
+    cudaError_t e = cudaMemcpyAsync(&word, ctx->scr.status, sizeof word, cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->scr.status, 0, sizeof word, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");
+    for (int code = 1; code < 32; ++code)
+        if (word & (1u << code)) {
+            ctx->err = code == MPPI_ERR_NUMERIC ? "every sample cost was non-finite"
+                                                : "device-side error";
+            return static_cast<mppi_status>(code);
+        }
+    return MPPI_OK;
+}
+
+const char *mppi_last_error(const mppi_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+mppi_status mppi_profile(mppi_ctx *ctx, int enable) {
+    if (!ctx) return MPPI_ERR_INVALID_ARG;
+    if (enable) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+        ctx->prof.launches.clear();
+        ctx->prof.pool_used = 0;
+    }
+    ctx->prof.on = enable != 0;
+    return MPPI_OK;
+}
+
+mppi_status mppi_profile_read(mppi_ctx *ctx, float *ms, int *launches) {
+    if (!ctx) return MPPI_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    float tot[MPPI_PROF_SLOTS] = {0};
+    int cnt[MPPI_PROF_SLOTS] = {0};
+    for (const auto &l : ctx->prof.launches) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, l.second.first, l.second.second);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "event elapsed time");
+        if (l.first >= 0 && l.first < MPPI_PROF_SLOTS) {
+            tot[l.first] += t;
+            cnt[l.first] += 1;
+        }
+    }
+    for (int i = 0; i < MPPI_PROF_SLOTS; ++i) {
+        if (ms) ms[i] = tot[i];
+        if (launches) launches[i] = cnt[i];
+    }
+    return MPPI_OK;
+}
+
+mppi_status mppi_sample_noise(uint64_t seed, uint64_t step, int K, int Q, uint32_t *bits_d,
+                              float *z_d, void *cuda_stream) {
+    if (K < 0 || Q < 0 || (!bits_d && !z_d)) return MPPI_ERR_INVALID_ARG;
+    if (static_cast<long long>(K) * Q > (1ll << 31) / 4) return MPPI_ERR_INVALID_ARG;
+    cudaError_t e = mppi::launch_sample_noise(seed, step, K, Q, bits_d, z_d,
+                                              static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
+}
+
+}  // extern "C"

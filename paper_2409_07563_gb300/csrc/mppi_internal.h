@@ -1,0 +1,105 @@
+// mppi_internal.h -- host-side context and the launch interfaces between the
+// C ABI (api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/mppi.h"
+
+namespace mppi {
+
+constexpr int kMaxNu = 8;
+constexpr int kMaxNx = 16;
+constexpr int kMaxTnu = 16384;
+constexpr int kMaxK = 1 << 24;
+constexpr int kUpdateThreads = 256;
+constexpr int kUpdateQb = 2;          // Philox blocks (4 elements each) per update block
+constexpr int kMaxUpdateChunks = 64;  // split-K factor cap of the update
+
+// Device scratch owned by a context.
+struct Scratch {
+    float *S = nullptr;                 // [K] trajectory costs
+    float *partials = nullptr;          // [3 * max rollout blocks] (rho_b, eta_b, eta2_b)
+    float *upartials = nullptr;         // [kMaxUpdateChunks * Q * 4] update partial sums
+    float *scalars = nullptr;           // [8] rho, eta, F, ess, valid
+    unsigned int *tickets = nullptr;    // [4] last-block tickets (self-resetting)
+    unsigned int *status = nullptr;     // [1] device status word
+    unsigned long long *counter = nullptr;    // [1] step counter
+    unsigned long long *last_step = nullptr;  // [1] step used by the latest mppi_step
+    float *ckpt = nullptr;              // adjoint checkpoints (lazily allocated)
+    size_t ckpt_floats = 0;
+    float *grad_partials = nullptr;     // adjoint block partials
+    size_t grad_partials_floats = 0;
+    float *io = nullptr;                // staging for mppi_step_host: x0, u_nom, u_new, stats
+};
+
+// Everything a rollout / update launch needs, passed by value.
+struct StepParams {
+    int K, T, nx, nu;
+    float dt, lambda, lam_beta;        // lam_beta = beta * lambda
+    float sigma[kMaxNu], ivar[kMaxNu];  // ivar = 1/sigma^2 (0 where sigma = 0)
+    uint64_t seed;
+    const float *x0, *u_nom;
+    float *u_new, *weights_out, *stats_out, *costs_out;
+    const float *dyn_params, *cost_params, *map;
+    int n_dyn_params, n_cost_params, map_h, map_w;
+    // scratch
+    float *S, *partials, *upartials, *scalars;
+    unsigned int *tickets, *status;
+    unsigned long long *counter, *last_step;
+};
+
+struct LaunchPlan {
+    int rollout_threads = 128;
+    int rollout_blocks = 1;
+    size_t rollout_smem = 0;
+    int update_qtiles = 1;
+    int update_chunks = 1;
+    int update_chunk_len = 256;
+};
+
+}  // namespace mppi
+
+// Event-pair record of kernel launches while profiling is on.
+struct ProfileRecord {
+    bool on = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> launches;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+};
+
+struct mppi_ctx {
+    int dyn_kind = 0, integrator = 0, nx = 0, nu = 0, cost_kind = 0;
+    int K = 0, T = 0, beta = 1, precision = 0, block_threads = 0;
+    float dt = 0.f, lambda = 1.f;
+    uint64_t seed = 0;
+    std::vector<float> sigma, dyn_params_h, cost_params_h;
+    float *d_dyn = nullptr, *d_cost = nullptr, *d_map = nullptr;
+    int map_h = 0, map_w = 0;
+    mppi::Scratch scr;
+    mppi::LaunchPlan plan;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    bool have_step = false;
+    std::string err;
+    ProfileRecord prof;
+};
+
+namespace mppi {
+
+// Kernel translation units (rollout.cu, update.cu, ...).
+bool rollout_supported(int dyn_kind, int cost_kind, int nx, int nu);
+size_t rollout_smem_bytes(const mppi_ctx &c);
+cudaError_t rollout_prepare(const mppi_ctx &c);  // sets smem attributes
+cudaError_t launch_rollout(const mppi_ctx &c, const StepParams &p);
+cudaError_t launch_update(const mppi_ctx &c, const StepParams &p);
+cudaError_t launch_sample_noise(uint64_t seed, uint64_t step, int K, int Q, uint32_t *bits,
+                                float *z, cudaStream_t s);
+cudaError_t launch_store_u64(unsigned long long *dst, unsigned long long v, cudaStream_t s);
+
+}  // namespace mppi

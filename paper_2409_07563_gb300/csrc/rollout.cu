@@ -1,0 +1,245 @@
+// rollout.cu -- fused noise + rollout + cost kernel (steps a1-a3) with the
+// weight-statistics reduction (step a4) folded into its tail.
+//
+// One sample per thread.  For every group of 4 time steps the thread draws
+// the group's Philox blocks (4*NU normals, Sec. II-C sampling of eps), then
+// runs x <- F(x, u + eps), J += l(x, v) - lambda I(v) (Algorithm 1 inner
+// loop) with state and cost in registers; J += phi(x) at the end.  Nothing
+// but S_k leaves the SM.  Each block then reduces its samples to
+// (rho_b, eta_b, eta2_b) relative to its own minimum; the last block to finish
+// (atomic ticket, no waiting) merges the partials with a log-sum-exp rescale
+// into rho, eta, F and ESS (Eq. 17-18 and Eq. 4).
+#include "device_common.cuh"
+#include "models.cuh"
+#include "mppi_internal.h"
+
+namespace mppi {
+namespace {
+
+constexpr int kRedFloats = 64;
+
+template <class Dyn, class Cost>
+struct Layout {
+    int u, dyn, cost, red, total;
+    __host__ __device__ Layout(int T, int n_dyn, int n_cost) {
+        u = 0;
+        dyn = round_up4(T * Dyn::NU);
+        cost = dyn + round_up4(Dyn::smem_floats(n_dyn));
+        red = cost + round_up4(Cost::smem_floats(n_cost));
+        total = red + kRedFloats;
+    }
+};
+
+// Merge of the per-block partials by the last block: rho = min rho_b,
+// eta = sum eta_b exp(-(rho_b - rho)/lambda), same for eta2 with 2/lambda.
+__device__ void finalize_weights(const StepParams &p, int nblocks, float *red) {
+    float rmin = __int_as_float(0x7f800000);
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        rmin = fminf(rmin, __ldcg(p.partials + 3 * b));
+    const float rho = block_min(rmin, red);
+    FloatPair e1{0.f, 0.f}, e2{0.f, 0.f};
+    if (is_finite(rho)) {
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+            const float rb = __ldcg(p.partials + 3 * b);
+            if (!is_finite(rb)) continue;
+            const float f = expf(-(rb - rho) / p.lambda);
+            e1 = pair_add(e1, FloatPair{__ldcg(p.partials + 3 * b + 1) * f, 0.f});
+            e2 = pair_add(e2, FloatPair{__ldcg(p.partials + 3 * b + 2) * f * f, 0.f});
+        }
+    }
+    const FloatPair eta = block_pair_sum(e1, red);
+    const FloatPair eta2 = block_pair_sum(e2, red);
+    if (threadIdx.x == 0) {
+        float F, ess, eta_v = eta.hi + eta.lo;
+        const bool ok = is_finite(rho) && eta_v > 0.f;
+        if (ok) {
+            F = rho - p.lambda * logf(eta_v / static_cast<float>(p.K));
+            ess = eta_v * eta_v / (eta2.hi + eta2.lo);
+        } else {
+            F = __int_as_float(0x7f800000);
+            ess = 0.f;
+            eta_v = 0.f;
+            atomicOr(p.status, 1u << MPPI_ERR_NUMERIC);
+        }
+        p.scalars[0] = ok ? rho : __int_as_float(0x7f800000);
+        p.scalars[1] = eta_v;
+        p.scalars[2] = F;
+        p.scalars[3] = ess;
+        p.scalars[4] = ok ? 1.f : 0.f;
+        if (p.stats_out) {
+            p.stats_out[0] = F;
+            p.stats_out[1] = p.scalars[0];
+            p.stats_out[2] = eta_v;
+            p.stats_out[3] = ess;
+        }
+        p.tickets[0] = 0u;  // ready for the next launch
+    }
+}
+
+template <class Dyn, class Cost>
+__global__ void __launch_bounds__(256) rollout_kernel(const StepParams p) {
+    constexpr int NX = Dyn::NX, NU = Dyn::NU;
+    extern __shared__ __align__(16) float smem[];
+    const Layout<Dyn, Cost> L(p.T, p.n_dyn_params, p.n_cost_params);
+    float *s_u = smem + L.u;
+    float *s_dyn = smem + L.dyn;
+    float *s_cost = smem + L.cost;
+    float *s_red = smem + L.red;
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < p.T * NU; i += nt) s_u[i] = p.u_nom[i];
+    Dyn::prepare(p.dyn_params, s_dyn, tid, nt);
+    Cost::prepare(p.cost_params, s_cost, tid, nt);
+    __syncthreads();
+
+    const NoiseKey nk = make_noise_key(p.seed, *p.counter);
+    const CostCtx cc{p.map, p.map_h, p.map_w};
+    float sig[NU], ivar[NU];
+#pragma unroll
+    for (int j = 0; j < NU; ++j) {
+        sig[j] = p.sigma[j];
+        ivar[j] = p.ivar[j];
+    }
+
+    const int k = blockIdx.x * nt + tid;
+    float S = __int_as_float(0x7f800000);  // inactive lanes take no part
+    if (k < p.K) {
+        float x[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) x[i] = p.x0[i];
+        CompSum J;
+        for (int t0 = 0; t0 < p.T; t0 += 4) {
+            float z[4 * NU];
+            group_normals<NU>(nk, static_cast<uint32_t>(k), t0, z);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int t = t0 + s;
+                if (t < p.T) {
+                    float v[NU];
+                    float is = 0.f;
+#pragma unroll
+                    for (int j = 0; j < NU; ++j) {
+                        const float u = s_u[t * NU + j];
+                        v[j] = u + sig[j] * z[s * NU + j];
+                        is += (v[j] - 0.5f * u) * (u * ivar[j]);
+                    }
+                    Dyn::step(x, v, s_dyn, p.dt);
+                    J.add(Cost::running(x, v, s_cost, cc) + p.lam_beta * is);
+                }
+            }
+        }
+        J.add(Cost::terminal(x, s_cost, cc));
+        S = J.value();
+        p.S[k] = S;
+    }
+
+    // ---- per-block weight statistics relative to the block minimum ----
+    const float Sf = is_finite(S) ? S : __int_as_float(0x7f800000);
+    const float rho_b = block_min(Sf, s_red);
+    float e = 0.f;
+    if (is_finite(Sf)) e = expf(-(Sf - rho_b) / p.lambda);
+    const FloatPair eta_b = block_pair_sum(FloatPair{e, 0.f}, s_red);
+    const FloatPair eta2_b = block_pair_sum(FloatPair{e * e, 0.f}, s_red);
+    __shared__ bool s_last;
+    if (tid == 0) {
+        p.partials[3 * blockIdx.x + 0] = rho_b;
+        p.partials[3 * blockIdx.x + 1] = eta_b.hi + eta_b.lo;
+        p.partials[3 * blockIdx.x + 2] = eta2_b.hi + eta2_b.lo;
+        __threadfence();
+        const unsigned int ticket = atomicAdd(p.tickets, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        finalize_weights(p, gridDim.x, s_red);
+    }
+}
+
+template <class Dyn, class Cost>
+size_t smem_bytes_for(const mppi_ctx &c) {
+    return sizeof(float) *
+           static_cast<size_t>(Layout<Dyn, Cost>(c.T, c.dyn_params_h.size(),
+                                                 c.cost_params_h.size()).total);
+}
+
+// Dispatch on (dynamics, cost).  F is called with a null pointer of the
+// kernel's template instance type pair.
+template <class F>
+bool dispatch(int dyn, int cost, int nx, int nu, F &&f) {
+    switch (dyn) {
+    case MPPI_DYN_CARTPOLE:
+        if (cost == MPPI_COST_QUADRATIC) return f((CartpoleDyn *)0, (QuadraticCost<4, 1> *)0);
+        return false;
+    case MPPI_DYN_QUADROTOR:
+        if (cost == MPPI_COST_QUADRATIC) return f((QuadrotorDyn *)0, (QuadraticCost<13, 4> *)0);
+        if (cost == MPPI_COST_QUAD_OBSTACLES) return f((QuadrotorDyn *)0, (QuadObstacleCost *)0);
+        return false;
+    case MPPI_DYN_BICYCLE_MLP:
+        if (cost == MPPI_COST_COSTMAP_SPEED) return f((BicycleMlpDyn *)0, (CostmapSpeedCost *)0);
+        if (cost == MPPI_COST_QUADRATIC) return f((BicycleMlpDyn *)0, (QuadraticCost<7, 2> *)0);
+        return false;
+    case MPPI_DYN_DOUBLE_INTEGRATOR:
+        if (cost == MPPI_COST_CIRCLE) return f((DoubleIntegratorDyn *)0, (CircleCost *)0);
+        if (cost == MPPI_COST_QUADRATIC)
+            return f((DoubleIntegratorDyn *)0, (QuadraticCost<4, 2> *)0);
+        return false;
+    case MPPI_DYN_LINEAR:
+        if (cost != MPPI_COST_QUADRATIC) return false;
+        if (nx == 2 && nu == 1) return f((LinearDyn<2, 1> *)0, (QuadraticCost<2, 1> *)0);
+        if (nx == 4 && nu == 2) return f((LinearDyn<4, 2> *)0, (QuadraticCost<4, 2> *)0);
+        if (nx == 6 && nu == 3) return f((LinearDyn<6, 3> *)0, (QuadraticCost<6, 3> *)0);
+        if (nx == 8 && nu == 4) return f((LinearDyn<8, 4> *)0, (QuadraticCost<8, 4> *)0);
+        return false;
+    default:
+        return false;
+    }
+}
+
+}  // namespace
+
+bool rollout_supported(int dyn_kind, int cost_kind, int nx, int nu) {
+    return dispatch(dyn_kind, cost_kind, nx, nu, [](auto *d, auto *) {
+        (void)d;
+        return true;
+    });
+}
+
+size_t rollout_smem_bytes(const mppi_ctx &c) {
+    size_t bytes = 0;
+    dispatch(c.dyn_kind, c.cost_kind, c.nx, c.nu, [&](auto *d, auto *cst) {
+        using D = std::remove_pointer_t<decltype(d)>;
+        using C = std::remove_pointer_t<decltype(cst)>;
+        bytes = smem_bytes_for<D, C>(c);
+        return true;
+    });
+    return bytes;
+}
+
+cudaError_t rollout_prepare(const mppi_ctx &c) {
+    cudaError_t err = cudaSuccess;
+    dispatch(c.dyn_kind, c.cost_kind, c.nx, c.nu, [&](auto *d, auto *cst) {
+        using D = std::remove_pointer_t<decltype(d)>;
+        using C = std::remove_pointer_t<decltype(cst)>;
+        err = cudaFuncSetAttribute(rollout_kernel<D, C>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(smem_bytes_for<D, C>(c)));
+        return true;
+    });
+    return err;
+}
+
+cudaError_t launch_rollout(const mppi_ctx &c, const StepParams &p) {
+    cudaError_t err = cudaErrorInvalidValue;
+    dispatch(c.dyn_kind, c.cost_kind, c.nx, c.nu, [&](auto *d, auto *cst) {
+        using D = std::remove_pointer_t<decltype(d)>;
+        using C = std::remove_pointer_t<decltype(cst)>;
+        rollout_kernel<D, C><<<c.plan.rollout_blocks, c.plan.rollout_threads,
+                               c.plan.rollout_smem, c.stream>>>(p);
+        err = cudaGetLastError();
+        return true;
+    });
+    return err;
+}
+
+}  // namespace mppi

@@ -1,0 +1,161 @@
+// update.cu -- weighted control update (step a5) and the noise diagnostic.
+//
+// u_new[e] = u_nom[e] + (sum_k exp(-(S_k - rho)/lambda) eps_{k,e}) / eta for every
+// flattened element e = t * nu + j (Algorithm 1, control update).  eps is
+// regenerated from the same Philox counter the rollout used (bit-identical
+// FP32 product sigma_j * z), never read from memory.  Grid: (Philox-block
+// tiles) x (sample chunks); each thread walks samples of its chunk, each
+// block reduces its partial sums, and the last block to finish (atomic
+// ticket) adds the chunks in a fixed order, so the result is deterministic.
+// Samples whose weight underflows to exactly zero contribute exactly zero and
+// are skipped.
+#include "device_common.cuh"
+#include "mppi_internal.h"
+
+namespace mppi {
+namespace {
+
+template <int NU>
+__global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams p, int chunk_len) {
+    constexpr int QB = kUpdateQb;
+    __shared__ float s_red[kUpdateThreads / kWarp][QB * 4];
+    __shared__ bool s_last;
+    const int TN = p.T * NU;
+    const int Q = (TN + 3) / 4;
+    const int q0 = blockIdx.x * QB;
+    const int k_begin = blockIdx.y * chunk_len;
+    const int k_end = min(p.K, k_begin + chunk_len);
+    const float rho = p.scalars[0], eta = p.scalars[1];
+    const bool valid = p.scalars[4] != 0.f;
+    const NoiseKey nk = make_noise_key(p.seed, *p.counter);
+
+    float acc[QB][4];
+#pragma unroll
+    for (int a = 0; a < QB; ++a)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[a][i] = 0.f;
+
+    for (int k = k_begin + threadIdx.x; k < k_end; k += blockDim.x) {
+        const float S = p.S[k];
+        float e = 0.f;
+        if (valid && is_finite(S)) e = expf(-(S - rho) / p.lambda);
+        if (blockIdx.x == 0) {
+            if (p.weights_out) p.weights_out[k] = valid ? e / eta : 0.f;
+            if (p.costs_out) p.costs_out[k] = S;
+        }
+        if (e == 0.f) continue;
+#pragma unroll
+        for (int a = 0; a < QB; ++a) {
+            const int q = q0 + a;
+            if (q < Q) {
+                float z[4];
+                box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(q)), z);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int el = 4 * q + i;
+                    const float eps = p.sigma[el % NU] * z[i];
+                    acc[a][i] += e * eps;
+                }
+            }
+        }
+    }
+
+    // block reduction of the QB*4 partial sums
+    const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
+#pragma unroll
+    for (int a = 0; a < QB; ++a)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float v = warp_sum(acc[a][i]);
+            if (lane == 0) s_red[wid][a * 4 + i] = v;
+        }
+    __syncthreads();
+    if (threadIdx.x < QB * 4) {
+        float v = 0.f;
+        for (int w = 0; w < kUpdateThreads / kWarp; ++w) v += s_red[w][threadIdx.x];
+        const int q = q0 + threadIdx.x / 4;
+        if (q < Q)
+            p.upartials[(static_cast<size_t>(blockIdx.y) * Q + q) * 4 + threadIdx.x % 4] = v;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int ticket = atomicAdd(p.tickets + 1, 1u);
+        s_last = (ticket == gridDim.x * gridDim.y - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+
+    // last block: combine chunks in order and write u_new
+    const float inv_eta = valid ? 1.f / eta : 0.f;
+    for (int el = threadIdx.x; el < TN; el += blockDim.x) {
+        float sum = 0.f;
+        for (int c = 0; c < static_cast<int>(gridDim.y); ++c)
+            sum += __ldcg(p.upartials + (static_cast<size_t>(c) * Q) * 4 + el);
+        p.u_new[el] = p.u_nom[el] + (valid ? sum * inv_eta : 0.f);
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long step = *p.counter;
+        *p.last_step = step;
+        *p.counter = step + 1ull;
+        p.tickets[1] = 0u;
+    }
+}
+
+__global__ void sample_noise_kernel(uint64_t seed, uint64_t step, int K, int Q, uint32_t *bits,
+                                    float *z) {
+    const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= static_cast<long long>(K) * Q) return;
+    const int k = static_cast<int>(idx / Q), q = static_cast<int>(idx % Q);
+    const NoiseKey nk = make_noise_key(seed, step);
+    const uint4 r = noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(q));
+    if (bits) {
+        bits[4 * idx + 0] = r.x;
+        bits[4 * idx + 1] = r.y;
+        bits[4 * idx + 2] = r.z;
+        bits[4 * idx + 3] = r.w;
+    }
+    if (z) {
+        float zz[4];
+        box_muller(r, zz);
+        for (int i = 0; i < 4; ++i) z[4 * idx + i] = zz[i];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_update(const mppi_ctx &c, const StepParams &p) {
+    const dim3 grid(c.plan.update_qtiles, c.plan.update_chunks);
+    const int len = c.plan.update_chunk_len;
+    switch (c.nu) {
+    case 1: update_kernel<1><<<grid, kUpdateThreads, 0, c.stream>>>(p, len); break;
+    case 2: update_kernel<2><<<grid, kUpdateThreads, 0, c.stream>>>(p, len); break;
+    case 3: update_kernel<3><<<grid, kUpdateThreads, 0, c.stream>>>(p, len); break;
+    case 4: update_kernel<4><<<grid, kUpdateThreads, 0, c.stream>>>(p, len); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_noise(uint64_t seed, uint64_t step, int K, int Q, uint32_t *bits,
+                                float *z, cudaStream_t s) {
+    const long long n = static_cast<long long>(K) * Q;
+    if (n == 0) return cudaSuccess;
+    const int threads = 256;
+    const long long blocks = (n + threads - 1) / threads;
+    sample_noise_kernel<<<static_cast<unsigned>(blocks), threads, 0, s>>>(seed, step, K, Q, bits, z);
+    return cudaGetLastError();
+}
+
+}  // namespace mppi
+
+namespace mppi {
+namespace {
+__global__ void store_u64_kernel(unsigned long long *dst, unsigned long long v) { *dst = v; }
+}  // namespace
+
+cudaError_t launch_store_u64(unsigned long long *dst, unsigned long long v, cudaStream_t s) {
+    store_u64_kernel<<<1, 1, 0, s>>>(dst, v);
+    return cudaGetLastError();
+}
+}  // namespace mppi

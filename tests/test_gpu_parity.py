@@ -1,0 +1,261 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bar (see the tolerance derivation in the design doc):
+  * Philox words bit-exact; normals within 8 ulp(|z|) + 2^-22;
+  * u_new within 1e-4 * sigma_j of the oracle for every (t, j) (FP32 path);
+  * stage-isolated: GPU weights / statistics from the GPU's own S_k agree with
+    the oracle's weighting of those S_k, and the GPU update agrees with the
+    oracle's FP64 noise weighted by those weights to 1e-5 * sigma_j.
+Inputs are seeded (workloads.py) and rounded to FP32 before either side sees
+them, so only the arithmetic differs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from _util import as_f32_problem, n_threads, with_
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def m():
+    if not torch.cuda.is_available():
+        pytest.fail("the -m gpu tests need a CUDA GPU")
+    import paper_2409_07563_gb300 as mod
+    mod.build()
+    return mod
+
+
+def run_gpu(m, p, step=0, ctl=None):
+    if ctl is None:
+        ctl = m.MPPI.from_problem(p)
+    if step:
+        ctl.counter = step
+    x0 = torch.tensor(p["x0"], dtype=torch.float32, device="cuda")
+    u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device="cuda")
+    out = ctl.step(x0, u, want_weights=True, want_costs=True)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy().astype(np.float64) for k, v in out.items()}
+    res["status"] = ctl.poll_status()
+    return res, ctl
+
+
+def compare(p, g, step=0, tol_sigma=1e-4, check_S=True):
+    """End-to-end and stage-isolated comparison; returns diagnostics."""
+    o = oracle.mppi_step(p, step=step, n_threads=n_threads(), want_eps=True)
+    lam = p["lam"]
+    sig = p["sigma"]
+    K = p["K"]
+    # stage-isolated weights from the GPU's costs
+    w_ref, st_ref, code = oracle.weights(g["costs"], lam)
+    assert code == 0
+    x = (g["costs"] - st_ref[1]) / lam
+    assert np.all(np.abs(g["weights"] - w_ref) <= 2e-5 * (1 + np.abs(x)) * w_ref + 1e-9)
+    assert g["stats"][1] == st_ref[1]                       # rho: min of the same floats
+    assert g["stats"][2] == pytest.approx(st_ref[2], rel=2e-5)
+    assert g["stats"][0] == pytest.approx(st_ref[0], rel=1e-6, abs=2e-5 * lam * np.log(K + 1))
+    assert g["stats"][3] == pytest.approx(st_ref[3], rel=1e-4)
+    # stage-isolated update: GPU weights' reference x oracle FP64 noise
+    u_iso = p["u_nom"] + np.einsum("k,ktj->tj", w_ref, o["eps"])
+    err_iso = np.abs(g["u_new"] - u_iso)
+    assert np.all(err_iso <= 1e-5 * sig[None, :] + 1e-7 * (sig[None, :] == 0)), \
+        f"update stage: max err/sigma {np.max(err_iso / np.maximum(sig, 1e-30))}"
+    # per-sample costs
+    dS = np.abs(g["costs"] - o["S"])
+    if check_S:
+        rel = dS / np.maximum(1.0, np.abs(o["S"]))
+        assert np.median(rel) < 1e-5, np.median(rel)
+    # end to end
+    err = np.abs(g["u_new"] - o["u_new"])
+    ratio = np.max(err / np.maximum(sig[None, :], 1e-30))
+    diag = dict(max_err_over_sigma=float(ratio), ess=float(o["stats"][3]),
+                max_dS_over_lambda=float(np.max(dS) / lam),
+                argmin_same=bool(np.argmin(g["costs"]) == np.argmin(o["S"])))
+    assert np.all(err <= tol_sigma * sig[None, :]), diag
+    return diag
+
+
+# --------------------------------------------------------------------------
+# noise
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed,step", [(0, 0), (20240911, 3), (2**40 + 17, 2**33 + 5),
+                                       (0xDEADBEEFCAFEBABE, 2**64 - 1)])
+def test_noise_bits_exact_and_normals(m, seed, step):
+    K, Q = 300, 37
+    bits = torch.empty(K * Q * 4, dtype=torch.int32, device="cuda")
+    z = torch.empty(K * Q * 4, dtype=torch.float32, device="cuda")
+    m.mppi_sample_noise(seed, step, K, Q, bits, z)
+    torch.cuda.synchronize()
+    gb = bits.cpu().numpy().view(np.uint32).reshape(K, Q, 4)
+    gz = z.cpu().numpy().astype(np.float64).reshape(K, Q, 4)
+    rng = np.random.default_rng(seed % 1000)
+    ks = np.concatenate([[0, K - 1], rng.integers(0, K, 60)])
+    for k in ks:
+        for q in range(Q):
+            ob, oz = oracle.noise_block(seed, step, int(k), q)
+            assert np.array_equal(gb[k, q], ob)
+            ulp = np.spacing(np.abs(oz).astype(np.float32)).astype(np.float64)
+            assert np.all(np.abs(gz[k, q] - oz) <= 8 * ulp + 2.0**-22), (k, q, gz[k, q], oz)
+
+
+# --------------------------------------------------------------------------
+# the three single-instance workloads at full size
+# --------------------------------------------------------------------------
+def test_cartpole_config_full(m):
+    p = as_f32_problem(W.cartpole())
+    g, ctl = run_gpu(m, p)
+    assert g["status"] == 0
+    compare(p, g)
+    # the next step uses the next counter value
+    g1, _ = run_gpu(m, p, ctl=ctl)
+    compare(p, g1, step=1)
+    assert not np.array_equal(g1["costs"], g["costs"])
+    assert ctl.counter == 2
+
+
+@pytest.mark.parametrize("lam", [10.0, 100.0, 1000.0])
+def test_cartpole_spread_weights(m, lam):
+    p = as_f32_problem(W.cartpole(lam=lam))
+    g, _ = run_gpu(m, p)
+    d = compare(p, g)
+    if lam >= 100:
+        assert d["ess"] > 10
+
+
+def test_quadrotor_config_full(m):
+    p = as_f32_problem(W.quadrotor())
+    g, _ = run_gpu(m, p)
+    compare(p, g)
+
+
+@pytest.mark.parametrize("lam", [200.0, 2000.0])
+def test_quadrotor_spread_weights_no_is(m, lam):
+    p = as_f32_problem(W.quadrotor(lam=lam, beta=0))
+    g, _ = run_gpu(m, p)
+    compare(p, g)
+
+
+def test_bicycle_mlp_fp32_config_full(m):
+    p = as_f32_problem(W.bicycle_mlp())
+    g, _ = run_gpu(m, p)
+    compare(p, g)
+
+
+# --------------------------------------------------------------------------
+# test models, ragged sizes (several blocks plus a partial one)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("K,T", [(1000, 37), (257, 5), (33, 101)])
+def test_cartpole_ragged(m, K, T):
+    p = as_f32_problem(W.cartpole(K=K, T=T, lam=20.0))
+    g, _ = run_gpu(m, p)
+    compare(p, g)
+
+
+@pytest.mark.parametrize("K,T", [(777, 23), (129, 150)])
+def test_quadrotor_ragged(m, K, T):
+    p = as_f32_problem(W.quadrotor(K=K, T=T, lam=300.0, beta=0))
+    g, _ = run_gpu(m, p)
+    compare(p, g)
+
+
+def test_bicycle_ragged(m):
+    p = as_f32_problem(W.bicycle_mlp(K=2001, T=21, lam=5.0))
+    g, _ = run_gpu(m, p)
+    compare(p, g)
+
+
+@pytest.mark.parametrize("cost", ["circle", "quadratic"])
+def test_double_integrator(m, cost):
+    p = as_f32_problem(W.double_integrator(K=333, T=50, cost=cost, lam=50.0))
+    g, _ = run_gpu(m, p)
+    compare(p, g)
+
+
+@pytest.mark.parametrize("nx,nu", [(2, 1), (4, 2), (6, 3), (8, 4)])
+def test_linear(m, nx, nu):
+    p = as_f32_problem(W.linear(K=300, T=30, nx=nx, nu=nu, lam=2.0))
+    g, _ = run_gpu(m, p)
+    compare(p, g)
+
+
+# --------------------------------------------------------------------------
+# edge cases
+# --------------------------------------------------------------------------
+def test_single_sample_single_step(m):
+    for K, T in [(1, 1), (1, 7), (5, 1), (2, 2)]:
+        p = as_f32_problem(W.quadrotor(K=K, T=T))
+        g, _ = run_gpu(m, p)
+        compare(p, g, check_S=True)
+        if K == 1:
+            assert g["weights"][0] == 1.0
+
+
+def test_zero_noise_returns_nominal_exactly(m):
+    base = W.double_integrator(K=100, T=20)
+    p = as_f32_problem(with_(base, sigma=[0.0, 0.0]))
+    g, _ = run_gpu(m, p)
+    assert np.array_equal(g["u_new"], p["u_nom"])
+
+
+def test_one_channel_without_noise(m):
+    base = W.quadrotor(K=500, T=30, lam=100.0, beta=0)
+    p = as_f32_problem(with_(base, sigma=[2.0, 0.0, 0.5, 0.0]))
+    g, _ = run_gpu(m, p)
+    compare(p, g)
+    assert np.array_equal(g["u_new"][:, 1], p["u_nom"][:, 1])
+
+
+def test_all_costs_non_finite(m):
+    base = W.cartpole(K=300, T=10)
+    p = as_f32_problem(with_(base, x0=[np.nan, 0, 0, 0]))
+    g, ctl = run_gpu(m, p)
+    assert g["status"] == 5                                  # MPPI_ERR_NUMERIC
+    assert np.array_equal(g["u_new"], p["u_nom"])
+    assert np.all(g["weights"] == 0)
+    assert np.isinf(g["stats"][0]) and np.isinf(g["stats"][1])
+    assert ctl.poll_status() == 0                            # cleared by the poll
+
+
+def test_determinism_and_counter(m):
+    p = as_f32_problem(W.cartpole(K=4096, T=100, lam=50.0))
+    ctl = m.MPPI.from_problem(p)
+    g0, _ = run_gpu(m, p, ctl=ctl)
+    ctl.counter = 0
+    g1, _ = run_gpu(m, p, ctl=ctl)
+    for key in ("u_new", "weights", "costs", "stats"):
+        assert np.array_equal(g0[key], g1[key]), key
+    ctl.counter = 2**40 + 3
+    g2, _ = run_gpu(m, p, ctl=ctl)
+    compare(p, g2, step=2**40 + 3)
+    assert ctl.counter == 2**40 + 4
+
+
+def test_in_place_update_and_host_entry(m):
+    p = as_f32_problem(W.quadrotor(K=1024, T=40, lam=200.0, beta=0))
+    ctl = m.MPPI.from_problem(p)
+    x0 = torch.tensor(p["x0"], dtype=torch.float32, device="cuda")
+    u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device="cuda")
+    ref = ctl.step(x0, u)["u_new"].reshape(-1).clone()
+    ctl.counter = 0
+    ctl.step_into(x0, u, u)                                  # u_new aliases u_nom
+    torch.cuda.synchronize()
+    assert torch.equal(u, ref)
+    ctl.counter = 0
+    u_host, stats = ctl.step_host(p["x0"], p["u_nom"])
+    assert np.array_equal(u_host.reshape(-1), ref.cpu().numpy())
+
+
+def test_invalid_arguments_are_rejected(m):
+    p = W.cartpole()
+    with pytest.raises(m.MPPIError):
+        m.MPPI.from_problem(p, lam=0.0)
+    with pytest.raises(m.MPPIError):
+        m.MPPI.from_problem(p, sigma=[-1.0])
+    with pytest.raises(m.MPPIError):
+        m.MPPI.from_problem(p, K=0)
+    with pytest.raises(m.MPPIError):
+        m.MPPI.from_problem(p, dyn_params=[1.0, 0.1, 0.5])
