@@ -44,8 +44,14 @@ def run_gpu(m, p, step=0, ctl=None):
     return res, ctl
 
 
-def compare(p, g, step=0, tol_sigma=1e-4, check_S=True):
-    """End-to-end and stage-isolated comparison; returns diagnostics."""
+def compare(p, g, step=0, tol_sigma=1e-4, check_S=True, cost_resolution=False):
+    """End-to-end and stage-isolated comparison; returns diagnostics.
+
+    cost_resolution=True widens the end-to-end bound by the first-order effect
+    of FP32 cost resolution, |du| <= 2 D / lambda * sum_k w_k |eps_k| with
+    D = 2^-17 max|S_k| (64 ulp of the largest cost), and checks that the
+    per-sample cost differences stay inside D (so the widening is not hiding
+    rollout drift)."""
     o = oracle.mppi_step(p, step=step, n_threads=n_threads(), want_eps=True)
     lam = p["lam"]
     sig = p["sigma"]
@@ -75,7 +81,12 @@ def compare(p, g, step=0, tol_sigma=1e-4, check_S=True):
     diag = dict(max_err_over_sigma=float(ratio), ess=float(o["stats"][3]),
                 max_dS_over_lambda=float(np.max(dS) / lam),
                 argmin_same=bool(np.argmin(g["costs"]) == np.argmin(o["S"])))
-    assert np.all(err <= tol_sigma * sig[None, :]), diag
+    bound = tol_sigma * sig[None, :]
+    if cost_resolution:
+        D = 2.0**-17 * np.max(np.abs(o["S"]))
+        assert np.mean(dS <= D) >= 0.99, (np.max(dS), D)
+        bound = bound + 2 * D / lam * np.einsum("k,ktj->tj", o["w"], np.abs(o["eps"]))
+    assert np.all(err <= bound), diag
     return diag
 
 
@@ -187,11 +198,21 @@ def test_linear(m, nx, nu):
 # --------------------------------------------------------------------------
 def test_single_sample_single_step(m):
     for K, T in [(1, 1), (1, 7), (5, 1), (2, 2)]:
-        p = as_f32_problem(W.quadrotor(K=K, T=T))
+        p = as_f32_problem(W.quadrotor(K=K, T=T, lam=50.0, beta=0))
         g, _ = run_gpu(m, p)
         compare(p, g, check_S=True)
         if K == 1:
             assert g["weights"][0] == 1.0
+
+
+def test_ill_conditioned_weights_fp32_cost_resolution(m):
+    # lambda = 0.5 against costs near 3e3 with two competing samples: FP32 holds
+    # S_k only to ~2.4e-4, i.e. 5e-4 lambda, so the bound widens by the
+    # cost-resolution term (see compare()).
+    for K, T in [(5, 1), (64, 3)]:
+        p = as_f32_problem(W.quadrotor(K=K, T=T))
+        g, _ = run_gpu(m, p)
+        compare(p, g, cost_resolution=True)
 
 
 def test_zero_noise_returns_nominal_exactly(m):
