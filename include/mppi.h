@@ -225,6 +225,36 @@ mppi_status mppi_profile_read(mppi_ctx *ctx, float *ms, int *launches);
 mppi_status mppi_sample_noise(uint64_t seed, uint64_t step, int K, int Q,
                               uint32_t *bits_d, float *z_d, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free weighting and update.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory, such as
+ * a real-time control thread (cudaMalloc may block for milliseconds) or a
+ * process whose device memory is fully reserved by another framework's pool.
+ * Given sample costs the caller computed (costs_d [K]; any sampler that uses
+ * the noise definition above with key `seed` and counter `step`), it runs
+ * steps (c) and (d) of mppi_step: rho, eta, F, ESS, the weights and
+ * u_new = u_nom + sum_k w_k eps_k, with eps regenerated from (seed, step) and
+ * sigma_h [nu] (host).  u_nom_d / u_new_d [T*nu], weights_d [K] and
+ * stats_d [4] = [F, rho, eta, ess] are device memory (weights_d, stats_d may
+ * be NULL).  Asynchronous on cuda_stream.
+ *
+ * It calls no cudaMalloc or cudaFree: its scratch is one fixed-size array in
+ * the library's device globals (about 265 KB, held by every GPU that loads
+ * the library until the process exits).  Limits: 1 <= K <= MPPI_NOALLOC_MAX_K,
+ * T * nu <= MPPI_NOALLOC_MAX_TNU, 1 <= nu <= 4; larger requests return
+ * MPPI_ERR_INVALID_ARG without touching the GPU.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents (the counters that must
+ * start at zero are cleared by each call), so calls that overlap on the GPU
+ * race: order them on one stream. */
+#define MPPI_NOALLOC_MAX_K 65536
+#define MPPI_NOALLOC_MAX_TNU 4096
+mppi_status mppi_update_noalloc(const float *costs_d, int K, int T, int nu, float lambda,
+                                const float *sigma_h, uint64_t seed, uint64_t step,
+                                const float *u_nom_d, float *u_new_d, float *weights_d,
+                                float *stats_d, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

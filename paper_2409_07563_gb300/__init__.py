@@ -18,7 +18,8 @@ from . import _build
 from ._lib import (MPPIError, CostDesc, DynamicsDesc, Options, check, load,  # noqa: F401
                    MPPI_PREC_FP32, MPPI_PREC_BF16_MLP)
 
-__all__ = ["build", "MPPI", "MPPIError", "mppi_sample_noise", "library_path"]
+__all__ = ["build", "MPPI", "MPPIError", "mppi_sample_noise", "mppi_update_noalloc",
+           "library_path"]
 
 library_path = _build.LIB_PATH
 
@@ -226,3 +227,33 @@ def mppi_sample_noise(seed, step, K, Q, bits=None, z=None, stream=None):
     st = L.mppi_sample_noise(int(seed) & (2**64 - 1), int(step) & (2**64 - 1), int(K), int(Q),
                              _dptr(bits), _dptr(z), _stream_handle(stream))
     check(st, "mppi_sample_noise")
+
+
+NOALLOC_MAX_K = 65536
+NOALLOC_MAX_TNU = 4096
+
+
+def mppi_update_noalloc(costs, lam, sigma, seed, step, u_nom, u_new, weights=None, stats=None,
+                        stream=None):
+    """Weights and control update from caller-computed costs without any device
+    allocation (``mppi_update_noalloc``), for callers that cannot allocate GPU
+    memory, e.g. a real-time control loop.  All tensors are caller-owned CUDA
+    float32; K <= 65536 and T * nu <= 4096."""
+    L = load()
+    K = costs.numel()
+    nu = len(sigma)
+    TN = u_nom.numel()
+    if K < 1 or K > NOALLOC_MAX_K or TN > NOALLOC_MAX_TNU or TN % nu:
+        raise MPPIError(1, "mppi_update_noalloc",
+                        f"K must be in [1, {NOALLOC_MAX_K}] and T*nu <= {NOALLOC_MAX_TNU}")
+    _check_tensor(costs, K, "costs")
+    _check_tensor(u_nom, TN, "u_nom")
+    _check_tensor(u_new, TN, "u_new")
+    _check_tensor(weights, K, "weights")
+    _check_tensor(stats, 4, "stats")
+    sig = _f32(sigma)
+    st = L.mppi_update_noalloc(_dptr(costs), K, TN // nu, nu, float(lam), _fptr(sig),
+                               int(seed) & (2**64 - 1), int(step) & (2**64 - 1), _dptr(u_nom),
+                               _dptr(u_new), _dptr(weights), _dptr(stats),
+                               _stream_handle(stream))
+    check(st, "mppi_update_noalloc")

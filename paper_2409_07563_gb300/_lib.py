@@ -97,8 +97,13 @@ def load() -> ctypes.CDLL:
 
 
 def _optional(L):
-    """Entry points added after the single-instance path (batched launch)."""
+    """Entry points added after the single-instance path."""
     vp, i = ctypes.c_void_p, ctypes.c_int
+    if hasattr(L, "mppi_update_noalloc"):
+        u64 = ctypes.c_uint64
+        L.mppi_update_noalloc.argtypes = [vp, i, i, i, ctypes.c_float, c_float_p, u64, u64,
+                                          vp, vp, vp, vp, vp]
+        L.mppi_update_noalloc.restype = ctypes.c_int
     if hasattr(L, "mppi_batch_create"):
         L.mppi_batch_create.argtypes = [i, ctypes.POINTER(InstanceDesc), ctypes.POINTER(Options),
                                         ctypes.POINTER(vp)]
