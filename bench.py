@@ -38,12 +38,27 @@ import workloads as W  # noqa: E402
 METRIC = "rollout-steps/sec (K*T per mppi_step)"
 UNIT = "rollout-steps/s"
 
-# Algorithmic FP32 operations per rollout-step of the quadrotor workload
-# (FMA = 2), counted from the formulas: RK4 (4 derivative evaluations of 60,
-# stage combinations 169, renormalisation 13) 422, quadratic cost 64, crash
-# test over 32 spheres 32 x 10, noise scaling + importance term 31, compensated
-# accumulation 4.  Transcendentals and the integer Philox work are not counted.
+# Algorithmic FP32 operations per rollout-step (FMA = 2), counted from the
+# formulas; transcendentals and the integer Philox work are not counted.
+#  quadrotor: RK4 (4 derivative evaluations of 60, stage combinations 169,
+#    renormalisation 13) 422, quadratic cost 64, crash test over 32 spheres
+#    32 x 10, noise scaling + importance term 31, compensated accumulation 4.
+#  cart-pole: Euler step 30, quadratic cost 14, noise + importance term 7,
+#    compensated accumulation 4.
+#  bicycle + MLP: MLP 2 (6*64 + 64*64 + 64*4) + 132 biases = 9604, kinematics
+#    and Euler 20, costmap bilinear + speed cost 15, noise + importance 14,
+#    compensated accumulation 4.
 QUAD_FLOPS_PER_ROLLOUT_STEP = 422 + 64 + 320 + 31 + 4
+FLOPS_PER_ROLLOUT_STEP = {
+    "quadrotor": QUAD_FLOPS_PER_ROLLOUT_STEP,
+    "cartpole": 30 + 14 + 7 + 4,
+    "bicycle": 9604 + 20 + 15 + 14 + 4,
+}
+KERNEL_NAME = {
+    "quadrotor": "quad_group_kernel<true> (four lanes per sample)",
+    "cartpole": "rollout_kernel<CartpoleDyn, QuadraticCost<4,1>>",
+    "bicycle": "rollout_kernel<BicycleMlpDyn, CostmapSpeedCost>",
+}
 # FP32 pipe: 128 FP32 lanes per SM, 2 flops per FMA.
 FP32_LANES_PER_SM = 128
 
@@ -180,8 +195,20 @@ def reference_arm(args, p):
     return 0
 
 
+def make_workload(name, K=None):
+    """The benchmark workloads; the quadrotor is the headline one."""
+    kw = {"K": K} if K else {}
+    if name == "quadrotor":
+        return W.quadrotor(**kw)
+    if name == "cartpole":
+        return W.cartpole(**kw)
+    if name == "bicycle":
+        return W.bicycle_mlp(**kw)
+    raise ValueError(name)
+
+
 def workload_config(p):
-    return {"workload": f"{p['name']} (quadrotor, RK4, 32 obstacles, lambda={p['lam']})",
+    return {"workload": f"{p['name']} (lambda={p['lam']}, seeded inputs)",
             "K": p["K"], "T": p["T"], "nx": p["nx"], "nu": p["nu"],
             "l2": "flushed by a 256 MiB write before every timed step"}
 
@@ -194,12 +221,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--K", type=int, default=None, help="override the sample count")
+    ap.add_argument("--workload", default="quadrotor", choices=sorted(FLOPS_PER_ROLLOUT_STEP),
+                    help="quadrotor (configuration 1, the headline) or a diagnostic run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
-    p = W.quadrotor()
-    if args.K:
-        p = W.quadrotor(K=args.K)
+    p = make_workload(args.workload, args.K)
     if args.impl == "reference":
         return reference_arm(args, p)
 
@@ -286,14 +313,14 @@ def main():
     roll_ms, roll_n = prof["rollout"]
     upd_ms, upd_n = prof["update"]
     roll_avg_ms = roll_ms / max(roll_n, 1)
-    achieved = QUAD_FLOPS_PER_ROLLOUT_STEP * rollout_steps / (roll_avg_ms * 1e-3) / 1e12
+    achieved = FLOPS_PER_ROLLOUT_STEP[args.workload] * rollout_steps / (roll_avg_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": "rollout_kernel<QuadrotorDyn, QuadObstacleCost>",
+                "kernel": KERNEL_NAME[args.workload],
                 "kernel_ms": roll_avg_ms, "update_kernel_ms": upd_ms / max(upd_n, 1),
                 "peak_note": (f"FP32 pipe: {props.multi_processor_count} SMs x 128 lanes x 2 "
                               f"x {sm_max:.0f} MHz (max SM clock)")}
-    traffic_file = os.path.join(ROOT, "profiles", "rollout_quadrotor_traffic.json")
+    traffic_file = os.path.join(ROOT, "profiles", f"rollout_{args.workload}_traffic.json")
     if os.path.exists(traffic_file):
         try:
             with open(traffic_file) as f:

@@ -16,9 +16,11 @@
  *   (d) u_new_t = u_t + sum_k w_k eps_{k,t}, w_k = exp(-(S_k - rho)/lambda)/eta
  *       (Algorithm 1, control update), with eps regenerated from the counter.
  *
- * Noise definition (the paper names no generator): element e = t*nu + j of
- * sample k is lane e % 4 of Philox4x32-10 block q = e / 4 with counter
- * (k, q, step_lo32, step_hi32) and key (seed_lo32, seed_hi32); lanes (0,1)
+ * Noise definition (the paper names no generator): with QT = ceil(T/4),
+ * element (t, j) of sample k is lane t % 4 of Philox4x32-10 block
+ * q = j*QT + t/4 (channel-major: one block = four consecutive steps of one
+ * control channel) with counter (k, q, step_lo32, step_hi32) and key
+ * (seed_lo32, seed_hi32); lanes (0,1)
  * and (2,3) are Box-Muller pairs: z_{2p} = sqrt(-2 ln u1) cos(2 pi u2),
  * z_{2p+1} = sqrt(-2 ln u1) sin(2 pi u2), u1 = ((r_{2p} >> 8) + 1) 2^-24,
  * u2 = (r_{2p+1} >> 8) 2^-24; eps = sigma_j z.  `step` is the context's
@@ -135,8 +137,10 @@ typedef struct {
     int beta;                 /* importance-sampling term: 1 (default) or 0 */
     int precision;            /* mppi_precision (default FP32) */
     uint64_t seed;            /* Philox key (default 0) */
-    int block_threads;        /* rollout block size; 0 = automatic */
-    int reserved[7];
+    int block_threads;        /* rollout block size (multiple of 32, <= 256); 0 = automatic */
+    int rollout_variant;      /* 0 automatic, 1 one sample per thread, 2 four lanes per
+                                 sample (QUADROTOR with at most 32 obstacles) */
+    int reserved[6];
 } mppi_options;
 
 /* Fills *opt with the defaults (beta 1, FP32, seed 0, automatic launch). */

@@ -25,9 +25,11 @@
  * Noise.  The paper names no generator (Sec. IV-C-3 only says samples are
  * drawn by the sampling distribution).  This project's definition:
  *
- *   element e = t*nu + j of sample k is lane (e mod 4) of Philox block
- *   q = floor(e / 4); counter = (k, q, step_lo32, step_hi32),
- *   key = (seed_lo32, seed_hi32);
+ *   channel-major layout: with T4 = 4 ceil(T / 4), element (t, j) of sample k
+ *   has index e = j T4 + t and is lane (e mod 4) of Philox block
+ *   q = floor(e / 4) = j T4/4 + floor(t / 4), i.e. one block holds four
+ *   consecutive time steps of one control channel;
+ *   counter = (k, q, step_lo32, step_hi32), key = (seed_lo32, seed_hi32);
  *   r = Philox4x32-10(counter, key);
  *   u_open(r) = ((r >> 8) + 1) * 2^-24  in (0, 1]
  *   u_half(r) = (r >> 8) * 2^-24        in [0, 1)
@@ -86,9 +88,10 @@ void oracle_noise_block(uint64_t seed, uint64_t step, uint32_t k, uint32_t q,
     }
 }
 
-static double normal_at(uint64_t seed, uint64_t step, int k, int t, int j, int nu)
+static double normal_at(uint64_t seed, uint64_t step, int k, int t, int j, int T)
 {
-    long e = (long)t * nu + j;
+    long T4 = 4L * ((T + 3) / 4);
+    long e = (long)j * T4 + t;
     double z[4];
     oracle_noise_block(seed, step, (uint32_t)k, (uint32_t)(e / 4), NULL, z);
     return z[e % 4];
@@ -99,7 +102,7 @@ void oracle_normals(uint64_t seed, uint64_t step, int K, int T, int nu, double *
     for (int k = 0; k < K; ++k)
         for (int t = 0; t < T; ++t)
             for (int j = 0; j < nu; ++j)
-                z[((long)k * T + t) * nu + j] = normal_at(seed, step, k, t, j, nu);
+                z[((long)k * T + t) * nu + j] = normal_at(seed, step, k, t, j, T);
 }
 
 /* ------------------------------------------------------------------------
@@ -489,7 +492,7 @@ int oracle_mppi_step(const oracle_problem *p, const double *x0, const double *u_
         double *v = (double *)malloc(sizeof(double) * TN);
         for (int t = 0; t < T; ++t)
             for (int j = 0; j < nu; ++j) {
-                ek[t * nu + j] = p->sigma[j] * normal_at(p->seed, p->step, k, t, j, nu);
+                ek[t * nu + j] = p->sigma[j] * normal_at(p->seed, p->step, k, t, j, T);
                 v[t * nu + j] = u_nom[t * nu + j] + ek[t * nu + j];
             }
         S[k] = oracle_rollout(p, x0, u_nom, v, NULL);

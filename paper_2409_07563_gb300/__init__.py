@@ -61,7 +61,7 @@ class MPPI:
 
     def __init__(self, *, dyn_kind, integrator, nx, nu, dyn_params, cost_kind, cost_params,
                  K, T, dt, lam, sigma, beta=1, seed=0, cost_map=None,
-                 precision=MPPI_PREC_FP32, block_threads=0):
+                 precision=MPPI_PREC_FP32, block_threads=0, rollout_variant=0):
         L = load()
         self._dyn_params = _f32(dyn_params)
         self._cost_params = _f32(cost_params)
@@ -81,6 +81,7 @@ class MPPI:
         opt.seed = int(seed) & (2**64 - 1)
         opt.precision = int(precision)
         opt.block_threads = int(block_threads)
+        opt.rollout_variant = int(rollout_variant)
         h = ctypes.c_void_p()
         st = L.mppi_create(ctypes.byref(dyn), ctypes.byref(cost), int(K), int(T), float(dt),
                            float(lam), _fptr(self._sigma), ctypes.byref(opt), ctypes.byref(h))

@@ -44,7 +44,8 @@ class CostDesc(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_int), ("precision", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("block_threads", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("block_threads", ctypes.c_int), ("rollout_variant", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class InstanceDesc(ctypes.Structure):

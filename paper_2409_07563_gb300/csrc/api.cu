@@ -95,16 +95,22 @@ void free_ctx(mppi_ctx *c) {
 
 void plan_launch(mppi_ctx &c) {
     mppi::LaunchPlan &pl = c.plan;
+    const bool group = mppi::quad_group_applicable(c) && c.variant_opt != mppi::kVariantGeneric;
+    pl.variant = group ? mppi::kVariantQuadGroup : mppi::kVariantGeneric;
+    const int lanes = group ? 4 : 1;             // threads per sample
+    const long threads_needed = static_cast<long>(c.K) * lanes;
     if (c.block_threads > 0) {
         pl.rollout_threads = c.block_threads;
+    } else if (group) {
+        pl.rollout_threads = 64;
     } else {
         // Spread samples over every SM first (the rollout is a serial chain per
         // sample, so more SMs beat more warps per SM at these sizes).
         const int per_sm = (c.K + c.num_sms - 1) / c.num_sms;
         pl.rollout_threads = std::min(128, std::max(32, ((per_sm + 31) / 32) * 32));
     }
-    pl.rollout_blocks = (c.K + pl.rollout_threads - 1) / pl.rollout_threads;
-    const int Q = (c.T * c.nu + 3) / 4;
+    pl.rollout_blocks = static_cast<int>((threads_needed + pl.rollout_threads - 1) / pl.rollout_threads);
+    const int Q = c.nu * ((c.T + 3) / 4);
     pl.update_qtiles = (Q + mppi::kUpdateQb - 1) / mppi::kUpdateQb;
     const int max_chunks =
         std::min(mppi::kMaxUpdateChunks, (c.K + mppi::kUpdateThreads - 1) / mppi::kUpdateThreads);
@@ -230,6 +236,11 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     if (o.beta != 0 && o.beta != 1) return MPPI_ERR_INVALID_ARG;
     if (o.block_threads < 0 || o.block_threads > 256 || o.block_threads % 32 != 0)
         return MPPI_ERR_INVALID_ARG;
+    if (o.rollout_variant < 0 || o.rollout_variant > 2) return MPPI_ERR_INVALID_ARG;
+    if (o.rollout_variant == 2 &&
+        (dyn->kind != MPPI_DYN_QUADROTOR ||
+         (cost->kind == MPPI_COST_QUAD_OBSTACLES && cost->n_params > 33 + 4 * 32)))
+        return MPPI_ERR_UNSUPPORTED;
     const int want_integrator = dyn->kind == MPPI_DYN_QUADROTOR ? MPPI_RK4 : MPPI_EULER;
     if (dyn->integrator != MPPI_EULER && dyn->integrator != MPPI_RK4) return MPPI_ERR_INVALID_ARG;
     if (dyn->integrator != want_integrator) return MPPI_ERR_UNSUPPORTED;
@@ -251,6 +262,7 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     c->beta = o.beta;
     c->precision = o.precision;
     c->block_threads = o.block_threads;
+    c->variant_opt = o.rollout_variant;
     c->dt = dt;
     c->lambda = lambda;
     c->seed = o.seed;
@@ -266,8 +278,8 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     }
     plan_launch(*c);
 
-    const int Q = (T * nu + 3) / 4;
-    const size_t max_blocks = (static_cast<size_t>(K) + 31) / 32;
+    const int Q = nu * ((T + 3) / 4);
+    const size_t max_blocks = (4 * static_cast<size_t>(K) + 31) / 32;  // 32-thread blocks, 4 lanes
     const size_t io_floats = static_cast<size_t>(nx) + 2 * static_cast<size_t>(T) * nu + 4;
     if ((e = dalloc(&c->scr.S, K)) != cudaSuccess ||
         (e = dalloc(&c->scr.partials, 3 * max_blocks)) != cudaSuccess ||
@@ -305,14 +317,17 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
         free_ctx(c);
         return MPPI_ERR_CUDA;
     }
-    c->plan.rollout_smem = mppi::rollout_smem_bytes(*c);
+    c->plan.rollout_smem = c->plan.variant == mppi::kVariantQuadGroup
+                               ? mppi::quad_group_smem_bytes(*c)
+                               : mppi::rollout_smem_bytes(*c);
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     if (c->plan.rollout_smem > static_cast<size_t>(max_smem)) {
         free_ctx(c);
         return MPPI_ERR_UNSUPPORTED;
     }
-    if ((e = mppi::rollout_prepare(*c)) != cudaSuccess) {
+    if ((e = mppi::rollout_prepare(*c)) != cudaSuccess ||
+        (c->plan.variant == mppi::kVariantQuadGroup && (e = mppi::quad_group_prepare(*c)) != cudaSuccess)) {
         free_ctx(c);
         return MPPI_ERR_CUDA;
     }
@@ -347,7 +362,8 @@ mppi_status mppi_step(mppi_ctx *ctx, const float *x0_d, const float *u_nom_d, fl
     cudaError_t e;
     {
         ProfScope ps(ctx, MPPI_PROF_ROLLOUT);
-        e = mppi::launch_rollout(*ctx, p);
+        e = ctx->plan.variant == mppi::kVariantQuadGroup ? mppi::launch_quad_group(*ctx, p)
+                                                         : mppi::launch_rollout(*ctx, p);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rollout launch");
     {

@@ -21,12 +21,14 @@ __host__ __device__ constexpr int round_up4(int n) { return (n + 3) & ~3; }
 // ---------------------------------------------------------------------------
 
 // Frictionless cart-pole, theta = 0 hanging down (Tedrake, Underactuated
-// Robotics): params [m_c, m_p, l, g].
+// Robotics): params [m_c, m_p, l, g]; shared copy adds 1/l at 4.
 struct CartpoleDyn {
     static constexpr int NX = 4, NU = 1;
-    __host__ __device__ static int smem_floats(int) { return 4; }
+    static constexpr bool kPipelineNoise = true;  // draw the next noise group early
+    __host__ __device__ static int smem_floats(int) { return 5; }
     __device__ static void prepare(const float *raw, float *s, int tid, int nt) {
         for (int i = tid; i < 4; i += nt) s[i] = raw[i];
+        if (tid == 0) s[4] = 1.0f / raw[2];
     }
     __device__ __forceinline__ static void step(float x[4], const float v[1], const float *P,
                                                 float dt) {
@@ -35,8 +37,9 @@ struct CartpoleDyn {
         sincosf(x[2], &s, &c);
         const float thd = x[3], f = v[0];
         const float D = m_c + m_p * s * s;
-        const float xdd = (f + m_p * s * (l * thd * thd + g * c)) / D;
-        const float thdd = (-f * c - m_p * l * thd * thd * c * s - (m_c + m_p) * g * s) / (l * D);
+        const float rD = __frcp_rn(D);  // correctly rounded 1/D, shared by both
+        const float xdd = (f + m_p * s * (l * thd * thd + g * c)) * rD;
+        const float thdd = (-f * c - m_p * l * thd * thd * c * s - (m_c + m_p) * g * s) * rD * P[4];
         x[0] += dt * x[1];
         x[1] += dt * xdd;
         x[2] += dt * thd;
@@ -48,6 +51,7 @@ struct CartpoleDyn {
 // params [m, Jxx, Jyy, Jzz, g]; shared copy [1/m, Jxx, Jyy, Jzz, g, 1/Jxx, 1/Jyy, 1/Jzz].
 struct QuadrotorDyn {
     static constexpr int NX = 13, NU = 4;
+    static constexpr bool kPipelineNoise = true;
     __host__ __device__ static int smem_floats(int) { return 8; }
     __device__ static void prepare(const float *raw, float *s, int tid, int) {
         if (tid == 0) {
@@ -120,6 +124,7 @@ struct QuadrotorDyn {
 // W3 @4608 (4x64), b3 @4864, L @4868 (16-byte aligned matrices).
 struct BicycleMlpDyn {
     static constexpr int NX = 7, NU = 2;
+    static constexpr bool kPipelineNoise = false;  // registers go to the MLP instead
     static constexpr int kW1 = 0, kB1 = 384, kW2 = 448, kB2 = 4544, kW3 = 4608, kB3 = 4864,
                          kL = 4868;
     __host__ __device__ static int smem_floats(int) { return 4872; }
@@ -178,6 +183,7 @@ struct BicycleMlpDyn {
 // 2-D double integrator: state [x, y, vx, vy], control [ax, ay].
 struct DoubleIntegratorDyn {
     static constexpr int NX = 4, NU = 2;
+    static constexpr bool kPipelineNoise = true;
     __host__ __device__ static int smem_floats(int) { return 0; }
     __device__ static void prepare(const float *, float *, int, int) {}
     __device__ __forceinline__ static void step(float x[4], const float v[2], const float *,
@@ -193,6 +199,7 @@ struct DoubleIntegratorDyn {
 template <int NX_, int NU_>
 struct LinearDyn {
     static constexpr int NX = NX_, NU = NU_;
+    static constexpr bool kPipelineNoise = true;
     __host__ __device__ static int smem_floats(int) { return NX * NX + NX * NU; }
     __device__ static void prepare(const float *raw, float *s, int tid, int nt) {
         for (int i = tid; i < NX * NX + NX * NU; i += nt) s[i] = raw[i];

@@ -54,7 +54,10 @@ struct StepParams {
     unsigned long long *counter, *last_step;
 };
 
+enum RolloutVariant { kVariantGeneric = 1, kVariantQuadGroup = 2 };
+
 struct LaunchPlan {
+    int variant = kVariantGeneric;
     int rollout_threads = 128;
     int rollout_blocks = 1;
     size_t rollout_smem = 0;
@@ -75,7 +78,7 @@ struct ProfileRecord {
 
 struct mppi_ctx {
     int dyn_kind = 0, integrator = 0, nx = 0, nu = 0, cost_kind = 0;
-    int K = 0, T = 0, beta = 1, precision = 0, block_threads = 0;
+    int K = 0, T = 0, beta = 1, precision = 0, block_threads = 0, variant_opt = 0;
     float dt = 0.f, lambda = 1.f;
     uint64_t seed = 0;
     std::vector<float> sigma, dyn_params_h, cost_params_h;
@@ -101,5 +104,10 @@ cudaError_t launch_update(const mppi_ctx &c, const StepParams &p);
 cudaError_t launch_sample_noise(uint64_t seed, uint64_t step, int K, int Q, uint32_t *bits,
                                 float *z, cudaStream_t s);
 cudaError_t launch_store_u64(unsigned long long *dst, unsigned long long v, cudaStream_t s);
+// rollout_quad.cu: four lanes per quadrotor sample
+bool quad_group_applicable(const mppi_ctx &c);
+size_t quad_group_smem_bytes(const mppi_ctx &c);
+cudaError_t quad_group_prepare(const mppi_ctx &c);
+cudaError_t launch_quad_group(const mppi_ctx &c, const StepParams &p);
 
 }  // namespace mppi

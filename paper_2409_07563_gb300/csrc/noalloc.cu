@@ -26,7 +26,7 @@ namespace {
 constexpr int kNaThreads = 256;
 constexpr int kNaMaxBlocks = MPPI_NOALLOC_MAX_K / kNaThreads;  // weight-reduction blocks
 constexpr int kNaChunks = 16;                                   // split-K factor of the update
-constexpr int kNaMaxQ = MPPI_NOALLOC_MAX_TNU / 4;
+constexpr int kNaMaxQ = MPPI_NOALLOC_MAX_TNU / 4 + 4;  // ceil(T/4) per channel
 constexpr int kNaQb = 2;
 
 // Layout of the scratch array, in floats.
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kNaThreads) na_update_kernel(const NaParams p,
     unsigned int *tickets = reinterpret_cast<unsigned int *>(p.scratch + kOffTickets);
     const float *scalars = p.scratch + kOffScalars;
     float *part = p.scratch + kOffUpdate;
-    const int TN = p.T * NU, Q = (TN + 3) / 4;
+    const int QT = (p.T + 3) / 4, Q = NU * QT;
     const int q0 = blockIdx.x * kNaQb;
     const int k_begin = blockIdx.y * chunk_len, k_end = min(p.K, k_begin + chunk_len);
     const float rho = scalars[0], eta = scalars[1];
@@ -138,8 +138,9 @@ __global__ void __launch_bounds__(kNaThreads) na_update_kernel(const NaParams p,
             if (q < Q) {
                 float z[4];
                 box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(q)), z);
+                const float sig = p.sigma[q / QT];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) acc[a][i] += e * (p.sigma[(4 * q + i) % NU] * z[i]);
+                for (int i = 0; i < 4; ++i) acc[a][i] += e * (sig * z[i]);
             }
         }
     }
@@ -166,10 +167,13 @@ __global__ void __launch_bounds__(kNaThreads) na_update_kernel(const NaParams p,
     if (!s_last) return;
     __threadfence();
     const float inv_eta = valid ? 1.f / eta : 0.f;
-    for (int el = threadIdx.x; el < TN; el += blockDim.x) {
+    for (int el = threadIdx.x; el < 4 * Q; el += blockDim.x) {
+        const int q = el / 4, j = q / QT, t = 4 * (q % QT) + el % 4;
+        if (t >= p.T) continue;
         float sum = 0.f;
         for (int c = 0; c < static_cast<int>(gridDim.y); ++c) sum += __ldcg(part + c * Q * 4 + el);
-        p.u_new[el] = p.u_nom[el] + (valid ? sum * inv_eta : 0.f);
+        const int o = t * NU + j;
+        p.u_new[o] = p.u_nom[o] + (valid ? sum * inv_eta : 0.f);
     }
 }
 
@@ -235,7 +239,7 @@ extern "C" mppi_status mppi_update_noalloc(const float *costs_d, int K, int T, i
     if (e != cudaSuccess) return MPPI_ERR_CUDA;
     const int nblocks = (K + kNaThreads - 1) / kNaThreads;
     na_weights_kernel<<<nblocks, kNaThreads, 0, s>>>(p);
-    const int Q = (T * nu + 3) / 4;
+    const int Q = nu * ((T + 3) / 4);
     const int qtiles = (Q + kNaQb - 1) / kNaQb;
     int chunks = std::min(kNaChunks, (K + kNaThreads - 1) / kNaThreads);
     const int chunk_len = (K + chunks - 1) / chunks;

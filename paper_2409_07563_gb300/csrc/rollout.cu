@@ -2,9 +2,10 @@
 // weight-statistics reduction (step a4) folded into its tail.
 //
 // One sample per thread.  For every group of 4 time steps the thread draws
-// the group's Philox blocks (4*NU normals, Sec. II-C sampling of eps), then
-// runs x <- F(x, u + eps), J += l(x, v) - lambda I(v) (Algorithm 1 inner
-// loop) with state and cost in registers; J += phi(x) at the end.  Nothing
+// one Philox block per control channel (4*NU normals, Sec. II-C sampling of
+// eps; drawn one group ahead), then runs x <- F(x, u + eps),
+// J += l(x, v) - lambda I(v) (Algorithm 1 inner loop) with state and cost in
+// registers; J += phi(x) at the end.  Nothing
 // but S_k leaves the SM.  Each block then reduces its samples to
 // (rho_b, eta_b, eta2_b) relative to its own minimum; the last block to finish
 // (atomic ticket, no waiting) merges the partials with a log-sum-exp rescale
@@ -12,11 +13,10 @@
 #include "device_common.cuh"
 #include "models.cuh"
 #include "mppi_internal.h"
+#include "rollout_tail.cuh"
 
 namespace mppi {
 namespace {
-
-constexpr int kRedFloats = 64;
 
 template <class Dyn, class Cost>
 struct Layout {
@@ -29,52 +29,6 @@ struct Layout {
         total = red + kRedFloats;
     }
 };
-
-// Merge of the per-block partials by the last block: rho = min rho_b,
-// eta = sum eta_b exp(-(rho_b - rho)/lambda), same for eta2 with 2/lambda.
-__device__ void finalize_weights(const StepParams &p, int nblocks, float *red) {
-    float rmin = __int_as_float(0x7f800000);
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-        rmin = fminf(rmin, __ldcg(p.partials + 3 * b));
-    const float rho = block_min(rmin, red);
-    FloatPair e1{0.f, 0.f}, e2{0.f, 0.f};
-    if (is_finite(rho)) {
-        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-            const float rb = __ldcg(p.partials + 3 * b);
-            if (!is_finite(rb)) continue;
-            const float f = expf(-(rb - rho) / p.lambda);
-            e1 = pair_add(e1, FloatPair{__ldcg(p.partials + 3 * b + 1) * f, 0.f});
-            e2 = pair_add(e2, FloatPair{__ldcg(p.partials + 3 * b + 2) * f * f, 0.f});
-        }
-    }
-    const FloatPair eta = block_pair_sum(e1, red);
-    const FloatPair eta2 = block_pair_sum(e2, red);
-    if (threadIdx.x == 0) {
-        float F, ess, eta_v = eta.hi + eta.lo;
-        const bool ok = is_finite(rho) && eta_v > 0.f;
-        if (ok) {
-            F = rho - p.lambda * logf(eta_v / static_cast<float>(p.K));
-            ess = eta_v * eta_v / (eta2.hi + eta2.lo);
-        } else {
-            F = __int_as_float(0x7f800000);
-            ess = 0.f;
-            eta_v = 0.f;
-            atomicOr(p.status, 1u << MPPI_ERR_NUMERIC);
-        }
-        p.scalars[0] = ok ? rho : __int_as_float(0x7f800000);
-        p.scalars[1] = eta_v;
-        p.scalars[2] = F;
-        p.scalars[3] = ess;
-        p.scalars[4] = ok ? 1.f : 0.f;
-        if (p.stats_out) {
-            p.stats_out[0] = F;
-            p.stats_out[1] = p.scalars[0];
-            p.stats_out[2] = eta_v;
-            p.stats_out[3] = ess;
-        }
-        p.tickets[0] = 0u;  // ready for the next launch
-    }
-}
 
 template <class Dyn, class Cost>
 __global__ void __launch_bounds__(256) rollout_kernel(const StepParams p) {
@@ -108,9 +62,16 @@ __global__ void __launch_bounds__(256) rollout_kernel(const StepParams p) {
 #pragma unroll
         for (int i = 0; i < NX; ++i) x[i] = p.x0[i];
         CompSum J;
+        const int QT = (p.T + 3) / 4;
+        // the next group's normals are drawn while this group integrates
+        // (software pipelining keeps Philox + Box-Muller off the state chain);
+        // the block drawn after the last group is never used
+        float z[4 * NU];
+        group_normals<NU>(nk, static_cast<uint32_t>(k), 0, QT, z);
         for (int t0 = 0; t0 < p.T; t0 += 4) {
-            float z[4 * NU];
-            group_normals<NU>(nk, static_cast<uint32_t>(k), t0, z);
+            float zn[4 * NU];
+            if (Dyn::kPipelineNoise)
+                group_normals<NU>(nk, static_cast<uint32_t>(k), t0 + 4, QT, zn);
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
                 const int t = t0 + s;
@@ -120,12 +81,18 @@ __global__ void __launch_bounds__(256) rollout_kernel(const StepParams p) {
 #pragma unroll
                     for (int j = 0; j < NU; ++j) {
                         const float u = s_u[t * NU + j];
-                        v[j] = u + sig[j] * z[s * NU + j];
+                        v[j] = u + sig[j] * z[4 * j + s];
                         is += (v[j] - 0.5f * u) * (u * ivar[j]);
                     }
                     Dyn::step(x, v, s_dyn, p.dt);
                     J.add(Cost::running(x, v, s_cost, cc) + p.lam_beta * is);
                 }
+            }
+            if (Dyn::kPipelineNoise) {
+#pragma unroll
+                for (int i = 0; i < 4 * NU; ++i) z[i] = zn[i];
+            } else if (t0 + 4 < p.T) {
+                group_normals<NU>(nk, static_cast<uint32_t>(k), t0 + 4, QT, z);
             }
         }
         J.add(Cost::terminal(x, s_cost, cc));
@@ -133,27 +100,7 @@ __global__ void __launch_bounds__(256) rollout_kernel(const StepParams p) {
         p.S[k] = S;
     }
 
-    // ---- per-block weight statistics relative to the block minimum ----
-    const float Sf = is_finite(S) ? S : __int_as_float(0x7f800000);
-    const float rho_b = block_min(Sf, s_red);
-    float e = 0.f;
-    if (is_finite(Sf)) e = expf(-(Sf - rho_b) / p.lambda);
-    const FloatPair eta_b = block_pair_sum(FloatPair{e, 0.f}, s_red);
-    const FloatPair eta2_b = block_pair_sum(FloatPair{e * e, 0.f}, s_red);
-    __shared__ bool s_last;
-    if (tid == 0) {
-        p.partials[3 * blockIdx.x + 0] = rho_b;
-        p.partials[3 * blockIdx.x + 1] = eta_b.hi + eta_b.lo;
-        p.partials[3 * blockIdx.x + 2] = eta2_b.hi + eta2_b.lo;
-        __threadfence();
-        const unsigned int ticket = atomicAdd(p.tickets, 1u);
-        s_last = (ticket == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        finalize_weights(p, gridDim.x, s_red);
-    }
+    block_weight_tail(p, S, s_red);
 }
 
 template <class Dyn, class Cost>

@@ -1,10 +1,11 @@
 // update.cu -- weighted control update (step a5) and the noise diagnostic.
 //
-// u_new[e] = u_nom[e] + (sum_k exp(-(S_k - rho)/lambda) eps_{k,e}) / eta for every
-// flattened element e = t * nu + j (Algorithm 1, control update).  eps is
-// regenerated from the same Philox counter the rollout used (bit-identical
-// FP32 product sigma_j * z), never read from memory.  Grid: (Philox-block
-// tiles) x (sample chunks); each thread walks samples of its chunk, each
+// u_new[t, j] = u_nom[t, j] + (sum_k exp(-(S_k - rho)/lambda) eps_{k,t,j}) / eta
+// for every (t, j) (Algorithm 1, control update).  eps is regenerated from the
+// same Philox counter the rollout used (bit-identical FP32 product
+// sigma_j * z), never read from memory: Philox block q holds channel
+// j = q / QT at steps 4 (q % QT) .. + 3.  Grid: (Philox-block tiles) x
+// (sample chunks); each thread walks samples of its chunk, each
 // block reduces its partial sums, and the last block to finish (atomic
 // ticket) adds the chunks in a fixed order, so the result is deterministic.
 // Samples whose weight underflows to exactly zero contribute exactly zero and
@@ -20,8 +21,8 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
     constexpr int QB = kUpdateQb;
     __shared__ float s_red[kUpdateThreads / kWarp][QB * 4];
     __shared__ bool s_last;
-    const int TN = p.T * NU;
-    const int Q = (TN + 3) / 4;
+    const int QT = (p.T + 3) / 4;
+    const int Q = NU * QT;
     const int q0 = blockIdx.x * QB;
     const int k_begin = blockIdx.y * chunk_len;
     const int k_end = min(p.K, k_begin + chunk_len);
@@ -50,12 +51,9 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
             if (q < Q) {
                 float z[4];
                 box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(q)), z);
+                const float sig = p.sigma[q / QT];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int el = 4 * q + i;
-                    const float eps = p.sigma[el % NU] * z[i];
-                    acc[a][i] += e * eps;
-                }
+                for (int i = 0; i < 4; ++i) acc[a][i] += e * (sig * z[i]);
             }
         }
     }
@@ -88,11 +86,14 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
 
     // last block: combine chunks in order and write u_new
     const float inv_eta = valid ? 1.f / eta : 0.f;
-    for (int el = threadIdx.x; el < TN; el += blockDim.x) {
+    for (int el = threadIdx.x; el < 4 * Q; el += blockDim.x) {
+        const int q = el / 4, j = q / QT, t = 4 * (q % QT) + el % 4;
+        if (t >= p.T) continue;
         float sum = 0.f;
         for (int c = 0; c < static_cast<int>(gridDim.y); ++c)
             sum += __ldcg(p.upartials + (static_cast<size_t>(c) * Q) * 4 + el);
-        p.u_new[el] = p.u_nom[el] + (valid ? sum * inv_eta : 0.f);
+        const int o = t * NU + j;
+        p.u_new[o] = p.u_nom[o] + (valid ? sum * inv_eta : 0.f);
     }
     if (threadIdx.x == 0) {
         const unsigned long long step = *p.counter;

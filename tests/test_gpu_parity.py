@@ -30,9 +30,9 @@ def m():
     return mod
 
 
-def run_gpu(m, p, step=0, ctl=None):
+def run_gpu(m, p, step=0, ctl=None, **kw):
     if ctl is None:
-        ctl = m.MPPI.from_problem(p)
+        ctl = m.MPPI.from_problem(p, **kw)
     if step:
         ctl.counter = step
     x0 = torch.tensor(p["x0"], dtype=torch.float32, device="cuda")
@@ -137,17 +137,38 @@ def test_cartpole_spread_weights(m, lam):
         assert d["ess"] > 10
 
 
-def test_quadrotor_config_full(m):
+@pytest.mark.parametrize("variant", [1, 2])
+def test_quadrotor_config_full(m, variant):
     p = as_f32_problem(W.quadrotor())
-    g, _ = run_gpu(m, p)
+    g, _ = run_gpu(m, p, rollout_variant=variant)
     compare(p, g)
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("lam", [200.0, 2000.0])
-def test_quadrotor_spread_weights_no_is(m, lam):
+def test_quadrotor_spread_weights_no_is(m, lam, variant):
     p = as_f32_problem(W.quadrotor(lam=lam, beta=0))
-    g, _ = run_gpu(m, p)
+    g, _ = run_gpu(m, p, rollout_variant=variant)
     compare(p, g)
+
+
+@pytest.mark.parametrize("threads", [32, 64, 128, 256])
+def test_quadrotor_lane_groups_block_sizes(m, threads):
+    # four lanes per sample; K not a multiple of the block's samples
+    p = as_f32_problem(W.quadrotor(K=1001, T=37, lam=300.0, beta=0))
+    g, _ = run_gpu(m, p, rollout_variant=2, block_threads=threads)
+    compare(p, g)
+
+
+def test_quadrotor_lane_groups_quadratic_cost_only(m):
+    base = W.quadrotor(K=700, T=50, lam=100.0, beta=1)
+    q = dict(base)
+    q["cost_kind"] = W.COST_QUADRATIC
+    q["cost_params"] = base["cost_params"][:31].copy()
+    p = as_f32_problem(q)
+    for variant in (1, 2):
+        g, _ = run_gpu(m, p, rollout_variant=variant)
+        compare(p, g)
 
 
 def test_bicycle_mlp_fp32_config_full(m):
@@ -166,10 +187,11 @@ def test_cartpole_ragged(m, K, T):
     compare(p, g)
 
 
-@pytest.mark.parametrize("K,T", [(777, 23), (129, 150)])
-def test_quadrotor_ragged(m, K, T):
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("K,T", [(777, 23), (129, 150), (3, 5)])
+def test_quadrotor_ragged(m, K, T, variant):
     p = as_f32_problem(W.quadrotor(K=K, T=T, lam=300.0, beta=0))
-    g, _ = run_gpu(m, p)
+    g, _ = run_gpu(m, p, rollout_variant=variant)
     compare(p, g)
 
 

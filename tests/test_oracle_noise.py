@@ -150,19 +150,20 @@ def test_normals_distribution(oracle_lib):
 
 
 def test_normals_layout_contract(oracle_lib):
-    # Element (k, t, j) is lane (t*nu + j) % 4 of Philox block q = (t*nu + j) // 4
-    # with counter (k, q, step_lo, step_hi): the project's definition that the
-    # CUDA path must reproduce bit for bit.
+    # Channel-major: with T4 = 4 ceil(T/4), element (k, t, j) is lane t % 4 of
+    # Philox block q = j T4/4 + t // 4 with counter (k, q, step_lo, step_hi):
+    # the project's definition that the CUDA path must reproduce bit for bit.
     seed, step = 2**40 + 17, 2**33 + 3
     for nu in (1, 2, 3, 4, 5):
-        K, T = 3, 7
-        z = oracle.normals(seed, step, K, T, nu)
-        for k in range(K):
-            for t in range(T):
-                for j in range(nu):
-                    e = t * nu + j
-                    _, blk = oracle.noise_block(seed, step, k, e // 4)
-                    assert z[k, t, j] == blk[e % 4]
+        for T in (1, 4, 7, 9):
+            K = 3
+            z = oracle.normals(seed, step, K, T, nu)
+            QT = (T + 3) // 4
+            for k in range(K):
+                for t in range(T):
+                    for j in range(nu):
+                        _, blk = oracle.noise_block(seed, step, k, j * QT + t // 4)
+                        assert z[k, t, j] == blk[t % 4]
 
 
 def test_noise_streams_differ(oracle_lib):
