@@ -18,8 +18,8 @@ from . import _build
 from ._lib import (MPPIError, CostDesc, DynamicsDesc, Options, check, load,  # noqa: F401
                    MPPI_PREC_FP32, MPPI_PREC_BF16_MLP)
 
-__all__ = ["build", "MPPI", "MPPIError", "mppi_sample_noise", "mppi_update_noalloc",
-           "library_path"]
+__all__ = ["build", "MPPI", "MPPIError", "MPPIStep", "mppi_sample_noise",
+           "mppi_update_noalloc", "library_path"]
 
 library_path = _build.LIB_PATH
 
@@ -258,3 +258,58 @@ def mppi_update_noalloc(costs, lam, sigma, seed, step, u_nom, u_new, weights=Non
                                _dptr(u_new), _dptr(weights), _dptr(stats),
                                _stream_handle(stream))
     check(st, "mppi_update_noalloc")
+
+
+# ---------------------------------------------------------------------------
+# differentiable step (cart-pole + quadratic cost + Euler)
+# ---------------------------------------------------------------------------
+def _theta_params(ctl_params, theta):
+    """Full (dyn_params, cost_params) device arrays with theta = (Q[4], R, l, m_c)
+    written into the cart-pole layouts [m_c, m_p, l, g] and [Q, R, goal, s]."""
+    import torch
+    dyn0, cost0 = ctl_params
+    dyn = torch.stack([theta[6], dyn0[1], theta[5], dyn0[3]])
+    cost = torch.cat([theta[0:5], cost0[5:]])
+    return dyn.contiguous(), cost.contiguous()
+
+
+class MPPIStep:
+    """``torch.autograd.Function`` over one MPPI step of a cart-pole context:
+    u_new = MPPIStep.apply(theta, x0, u_nom, ctl) with theta = (Q[4], R, l, m_c)
+    as a CUDA float32 tensor.  The backward calls ``mppi_step_backward`` (the
+    adjoint kernels) at the same noise; call it before the next step on ``ctl``.
+    """
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, theta, x0, u_nom, ctl):
+        if cls._fn is None:
+            cls._fn = _make_step_function()
+        return cls._fn.apply(theta, x0, u_nom, ctl)
+
+
+def _make_step_function():
+    import torch
+
+    class _Step(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, theta, x0, u_nom, ctl):
+            th = theta.detach().to(torch.float32).contiguous()
+            base = (torch.tensor(ctl._dyn_params, device=th.device),
+                    torch.tensor(ctl._cost_params, device=th.device))
+            dyn, cost = _theta_params(base, th)
+            ctl.set_params(dyn.cpu().numpy(), cost.cpu().numpy())
+            out = ctl.step(x0, u_nom)
+            ctx.ctl = ctl
+            ctx.counter = ctl.counter
+            return out["u_new"]
+
+        @staticmethod
+        def backward(ctx, grad_u_new):
+            if ctx.ctl.counter != ctx.counter:
+                raise RuntimeError("MPPIStep.backward: the context stepped again after forward")
+            g = ctx.ctl.backward(grad_u_new.contiguous().to(torch.float32))
+            return g, None, None, None
+
+    return _Step

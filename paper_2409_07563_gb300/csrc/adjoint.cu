@@ -1,0 +1,308 @@
+// adjoint.cu -- gradient of an MPPI step w.r.t. cost weights and dynamics
+// parameters at fixed noise (step a8), cart-pole + quadratic cost + Euler.
+//
+// L = sum_{t,j} G_{t,j} u_new[t,j] with u_new = u + sum_k w_k eps_k and
+// w = softmax(-S / lambda) (Algorithm 1's weights), so
+//   dL/dw_k = a_k = sum G eps_k,   dL/dS_k = -(w_k / lambda)(a_k - sum_i w_i a_i),
+//   dL/dtheta = sum_k dL/dS_k dS_k/dtheta = -(1/lambda) Cov_w(a, g),  g_k = dS_k/dtheta.
+// The covariance is formed around the arg-min sample k* (a_ref = a_k*,
+// g_ref = g_k*): Cov_w = sum w Da Dg - (sum w Da)(sum w Dg) with Da = a - a_ref.
+// With saturated weights (one sample carrying nearly all the weight) the
+// direct form a_k - sum_i w_i a_i cancels catastrophically in FP32; the
+// centred form only ever subtracts nearby trajectories' values.
+// dS_k/dtheta for theta = (Q[0..3], R, l, m_c):
+//   Q_i and R enter the running and terminal costs directly (sums over the
+//   trajectory, accumulated on a forward sweep);
+//   l and m_c enter through the dynamics: a reverse (adjoint) sweep
+//   lam_T = dphi/dx_T + dl/dx_T, lam_t = (I + dt df/dx)^T lam_{t+1} + dl/dx_t,
+//   dS/dp += dt lam_{t+1}^T df/dp(x_t, v_t).
+// Memory is O(sqrt T) per sample: the forward sweep stores the state every
+// C = ceil(sqrt T) steps; the reverse sweep recomputes each segment from its
+// checkpoint into a per-thread buffer and walks it backwards.  Samples whose
+// dL/dS_k is exactly zero (weight underflowed) contribute exactly zero and
+// skip the sweep.  Three kernels: forward sweep (checkpoints, a_k, direct
+// derivatives, k*), reverse sweep (adjoint derivatives), centred reduction.
+#include "device_common.cuh"
+#include "models.cuh"
+#include "mppi_internal.h"
+
+namespace mppi {
+namespace {
+
+constexpr int kAdjThreads = 128;
+
+struct CartpoleJac {
+    // df/dx entries that are not 0/1 and df/d(l, m_c) of xdd (row 1) and thdd (row 3)
+    float xdd_th, xdd_w, thdd_th, thdd_w;
+    float xdd_l, xdd_mc, thdd_l, thdd_mc;
+};
+
+// Partial derivatives of xdd = N1 / D and thdd = N2 / (l D) for the cart-pole
+// with theta = 0 hanging down, D = m_c + m_p s^2,
+// N1 = f + m_p s (l w^2 + g c), N2 = -f c - m_p l w^2 c s - (m_c + m_p) g s.
+__device__ __forceinline__ CartpoleJac cartpole_jac(const float *P, float th, float w, float f) {
+    const float m_c = P[0], m_p = P[1], l = P[2], g = P[3];
+    float s, c;
+    sincosf(th, &s, &c);
+    const float w2 = w * w;
+    const float D = m_c + m_p * s * s;
+    const float iD = 1.0f / D, il = 1.0f / l;
+    const float N1 = f + m_p * s * (l * w2 + g * c);
+    const float N2 = -f * c - m_p * l * w2 * c * s - (m_c + m_p) * g * s;
+    const float dD_th = 2.0f * m_p * s * c;
+    const float dN1_th = m_p * (c * (l * w2 + g * c) - g * s * s);
+    const float dN1_w = 2.0f * m_p * s * l * w;
+    const float dN1_l = m_p * s * w2;
+    const float dN2_th = f * s - m_p * l * w2 * (c * c - s * s) - (m_c + m_p) * g * c;
+    const float dN2_w = -2.0f * m_p * l * w * c * s;
+    const float dN2_l = -m_p * w2 * c * s;
+    const float dN2_mc = -g * s;
+    CartpoleJac J;
+    J.xdd_th = (dN1_th - N1 * iD * dD_th) * iD;
+    J.xdd_w = dN1_w * iD;
+    J.xdd_l = dN1_l * iD;
+    J.xdd_mc = -N1 * iD * iD;
+    J.thdd_th = (dN2_th - N2 * iD * dD_th) * iD * il;
+    J.thdd_w = dN2_w * iD * il;
+    J.thdd_l = (dN2_l - N2 * il) * iD * il;
+    J.thdd_mc = (dN2_mc - N2 * iD) * iD * il;
+    return J;
+}
+
+// Weight of sample k from the forward step's statistics (0 when non-finite).
+__device__ __forceinline__ float weight_of(const StepParams &p, int k) {
+    const float rho = p.scalars[0], eta = p.scalars[1];
+    const float S = p.S[k];
+    if (p.scalars[4] == 0.f || !is_finite(S)) return 0.f;
+    return expf(-(S - rho) / p.lambda) / eta;
+}
+
+struct AdjParams {
+    StepParams sp;
+    const float *G;          // dL/du_new [T]
+    const float *x0, *u_nom; // inputs of the forward step (saved copies)
+    float *ckpt;             // [nck][4][K]
+    float *per_sample;       // [8][K]: a_k, dS/dQ0..3, dS/dR, dS/dl, dS/dm_c
+    int *kref;               // arg-min sample index
+    float *bpart;            // block partials
+    float *grad_out;         // [7]
+    int C, nck;
+};
+
+// Forward sweep: checkpoints, direct derivatives dS/dQ, dS/dR, a_k, and k*.
+__global__ void __launch_bounds__(kAdjThreads) adjoint_forward_kernel(const AdjParams a) {
+    const StepParams &p = a.sp;
+    __shared__ float s_par[8];
+    if (threadIdx.x < 4) s_par[threadIdx.x] = p.dyn_params[threadIdx.x];
+    if (threadIdx.x == 0) s_par[4] = 1.0f / p.dyn_params[2];
+    __syncthreads();
+    const float *C = p.cost_params;  // Q(4), R(1), goal(4), s
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const NoiseKey nk = make_noise_key(p.seed, *p.last_step);
+    const int K = p.K, T = p.T;
+    if (k < K) {
+        float x[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = a.x0[i];
+        float dQ[4] = {0.f, 0.f, 0.f, 0.f}, dR = 0.f, ak = 0.f;
+        const float sig = p.sigma[0];
+        float z[4];
+        for (int t = 0; t < T; ++t) {
+            if (t % a.C == 0) {
+                const int c = t / a.C;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a.ckpt[(static_cast<size_t>(c) * 4 + i) * K + k] = x[i];
+            }
+            if ((t & 3) == 0) box_muller(noise_bits(nk, static_cast<uint32_t>(k), t / 4), z);
+            const float eps = sig * z[t & 3];
+            const float v = a.u_nom[t] + eps;
+            ak += a.G[t] * eps;
+            CartpoleDyn::step(x, &v, s_par, p.dt);
+            dR += v * v;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float d = x[i] - C[5 + i];
+                dQ[i] += d * d;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float d = x[i] - C[5 + i];
+            dQ[i] += C[9] * d * d;
+        }
+        a.per_sample[0 * K + k] = ak;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a.per_sample[(1 + i) * K + k] = dQ[i];
+        a.per_sample[5 * K + k] = dR;
+        // arg-min sample (smallest index among exact minima) as reference
+        if (p.scalars[4] != 0.f && p.S[k] == p.scalars[0]) atomicMin(a.kref, k);
+    }
+}
+
+constexpr int kMaxSeg = 128;  // C = ceil(sqrt T) <= 128 for T <= 16384
+
+// Reverse sweep of every sample with non-zero weight: dS_k/dl, dS_k/dm_c.
+__global__ void __launch_bounds__(kAdjThreads) adjoint_reverse_kernel(const AdjParams a) {
+    const StepParams &p = a.sp;
+    __shared__ float s_par[8];
+    if (threadIdx.x < 4) s_par[threadIdx.x] = p.dyn_params[threadIdx.x];
+    if (threadIdx.x == 0) s_par[4] = 1.0f / p.dyn_params[2];
+    __syncthreads();
+    const float *C = p.cost_params;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int K = p.K, T = p.T;
+    const NoiseKey nk = make_noise_key(p.seed, *p.last_step);
+    if (k < K) {
+        if (weight_of(p, k) != 0.f) {
+            const float Q[4] = {C[0], C[1], C[2], C[3]};
+            const float gl[4] = {C[5], C[6], C[7], C[8]};
+            const float s_term = C[9], sig = p.sigma[0], dt = p.dt;
+            float xs[kMaxSeg + 1][4];
+            float vs[kMaxSeg];
+            // adjoint at x_T: terminal cost and the last running cost
+            float lam[4];
+            float gl_p = 0.f, gmc = 0.f;
+            bool first = true;
+            for (int c = a.nck - 1; c >= 0; --c) {
+                const int t_begin = c * a.C, t_end = min(T, t_begin + a.C);
+                // recompute the segment's states and controls from its checkpoint
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    xs[0][i] = a.ckpt[(static_cast<size_t>(c) * 4 + i) * K + k];
+                float z[4];
+                for (int t = t_begin; t < t_end; ++t) {
+                    if (t == t_begin || (t & 3) == 0)
+                        box_muller(noise_bits(nk, static_cast<uint32_t>(k), t / 4), z);
+                    const float v = a.u_nom[t] + sig * z[t & 3];
+                    vs[t - t_begin] = v;
+                    float x[4] = {xs[t - t_begin][0], xs[t - t_begin][1], xs[t - t_begin][2],
+                                  xs[t - t_begin][3]};
+                    CartpoleDyn::step(x, &v, s_par, dt);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) xs[t - t_begin + 1][i] = x[i];
+                }
+                if (first) {
+                    const int n = t_end - t_begin;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        lam[i] = 2.0f * (1.0f + s_term) * Q[i] * (xs[n][i] - gl[i]);
+                    first = false;
+                }
+                for (int t = t_end - 1; t >= t_begin; --t) {
+                    const int o = t - t_begin;
+                    const CartpoleJac J = cartpole_jac(s_par, xs[o][2], xs[o][3], vs[o]);
+                    // parameter gradient through x_{t+1} = x_t + dt f(x_t, v_t)
+                    gl_p += dt * (lam[1] * J.xdd_l + lam[3] * J.thdd_l);
+                    gmc += dt * (lam[1] * J.xdd_mc + lam[3] * J.thdd_mc);
+                    // lam_t = (I + dt df/dx)^T lam_{t+1}
+                    const float l0 = lam[0], l1 = lam[1], l2 = lam[2], l3 = lam[3];
+                    lam[1] = l1 + dt * l0;
+                    lam[2] = l2 + dt * (l1 * J.xdd_th + l3 * J.thdd_th);
+                    lam[3] = l3 + dt * (l2 + l1 * J.xdd_w + l3 * J.thdd_w);
+                    lam[0] = l0;
+                    if (t >= 1) {  // running cost of step t-1 sits on x_t
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) lam[i] += 2.0f * Q[i] * (xs[o][i] - gl[i]);
+                    }
+                }
+            }
+            a.per_sample[6 * K + k] = gl_p;
+            a.per_sample[7 * K + k] = gmc;
+        }
+    }
+}
+
+// dL/dtheta = -(1/lambda) [sum w Da Dg - (sum w Da)(sum w Dg)] around k*,
+// block partials merged in a fixed order by the last block.
+__global__ void __launch_bounds__(kAdjThreads) adjoint_reduce_kernel(const AdjParams a) {
+    const StepParams &p = a.sp;
+    __shared__ float s_red[64];
+    __shared__ bool s_last;
+    const int K = p.K;
+    const int kr = *a.kref;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    float v[15];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) v[i] = 0.f;
+    if (k < K && kr < K) {
+        const float w = weight_of(p, k);
+        if (w != 0.f) {
+            const float da = a.per_sample[k] - a.per_sample[kr];
+            v[0] = w * da;
+#pragma unroll
+            for (int i = 0; i < 7; ++i) {
+                const float dg = a.per_sample[(1 + i) * K + k] - a.per_sample[(1 + i) * K + kr];
+                v[1 + i] = w * dg;
+                v[8 + i] = w * da * dg;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 15; ++i) {
+        const FloatPair t = block_pair_sum(FloatPair{v[i], 0.f}, s_red);
+        if (threadIdx.x == 0) a.bpart[15 * blockIdx.x + i] = t.hi + t.lo;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(p.tickets + 3, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    float tot[15];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) {
+        FloatPair acc{0.f, 0.f};
+        for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += blockDim.x)
+            acc = pair_add(acc, FloatPair{__ldcg(a.bpart + 15 * b + i), 0.f});
+        const FloatPair t = block_pair_sum(acc, s_red);
+        tot[i] = t.hi + t.lo;
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i)
+            a.grad_out[i] = (kr < K) ? -(tot[8 + i] - tot[0] * tot[1 + i]) / p.lambda : 0.f;
+        p.tickets[3] = 0u;
+    }
+}
+
+}  // namespace
+
+size_t adjoint_scratch_floats(int K, int T) {
+    int C = 1;
+    while (C * C < T) ++C;
+    const int nck = (T + C - 1) / C;
+    const int blocks = (K + kAdjThreads - 1) / kAdjThreads;
+    return static_cast<size_t>(nck) * 4 * K + 8 * static_cast<size_t>(K) + 15 * blocks + 4;
+}
+
+cudaError_t launch_adjoint(const mppi_ctx &c, const StepParams &sp, const float *G,
+                           const float *x0, const float *u_nom, float *scratch,
+                           float *grad_out, cudaStream_t s) {
+    AdjParams a;
+    a.sp = sp;
+    a.G = G;
+    a.x0 = x0;
+    a.u_nom = u_nom;
+    int C = 1;
+    while (C * C < c.T) ++C;
+    if (C > kMaxSeg) return cudaErrorInvalidValue;
+    a.C = C;
+    a.nck = (c.T + C - 1) / C;
+    a.ckpt = scratch;
+    a.per_sample = a.ckpt + static_cast<size_t>(a.nck) * 4 * c.K;
+    const int blocks = (c.K + kAdjThreads - 1) / kAdjThreads;
+    a.bpart = a.per_sample + 8 * static_cast<size_t>(c.K);
+    a.kref = reinterpret_cast<int *>(a.bpart + 15 * blocks);
+    a.grad_out = grad_out;
+    cudaError_t e = cudaMemsetAsync(a.kref, 0x7f, sizeof(int), s);  // "no reference yet"
+    if (e != cudaSuccess) return e;
+    adjoint_forward_kernel<<<blocks, kAdjThreads, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    adjoint_reverse_kernel<<<blocks, kAdjThreads, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    adjoint_reduce_kernel<<<blocks, kAdjThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mppi

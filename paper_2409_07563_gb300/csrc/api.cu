@@ -87,7 +87,8 @@ void free_ctx(mppi_ctx *c) {
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     void *ptrs[] = {c->d_dyn, c->d_cost, c->d_map, c->scr.S, c->scr.partials, c->scr.upartials,
                     c->scr.scalars, c->scr.tickets, c->scr.status, c->scr.counter,
-                    c->scr.last_step, c->scr.ckpt, c->scr.grad_partials, c->scr.io};
+                    c->scr.last_step, c->scr.ckpt, c->scr.grad_partials, c->scr.io,
+                    c->scr.saved_in, c->scr.adj};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -150,6 +151,7 @@ StepParams make_params(const mppi_ctx &c) {
     p.status = c.scr.status;
     p.counter = c.scr.counter;
     p.last_step = c.scr.last_step;
+    p.saved_in = c.differentiable ? c.scr.saved_in : nullptr;
     return p;
 }
 
@@ -277,6 +279,8 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
         return MPPI_ERR_CUDA;
     }
     plan_launch(*c);
+    c->differentiable = dyn->kind == MPPI_DYN_CARTPOLE && cost->kind == MPPI_COST_QUADRATIC &&
+                        dyn->integrator == MPPI_EULER;
 
     const int Q = nu * ((T + 3) / 4);
     const size_t max_blocks = (4 * static_cast<size_t>(K) + 31) / 32;  // 32-thread blocks, 4 lanes
@@ -290,6 +294,9 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
         (e = dalloc(&c->scr.counter, 1)) != cudaSuccess ||
         (e = dalloc(&c->scr.last_step, 1)) != cudaSuccess ||
         (e = dalloc(&c->scr.io, io_floats)) != cudaSuccess ||
+        (c->differentiable &&
+         (e = dalloc(&c->scr.saved_in, static_cast<size_t>(nx) + static_cast<size_t>(T) * nu)) !=
+             cudaSuccess) ||
         (e = dalloc(&c->d_dyn, c->dyn_params_h.size())) != cudaSuccess ||
         (e = dalloc(&c->d_cost, c->cost_params_h.size())) != cudaSuccess) {
         free_ctx(c);
@@ -431,9 +438,31 @@ mppi_status mppi_set_params(mppi_ctx *ctx, const float *dyn_params, const float 
 
 mppi_status mppi_step_backward(mppi_ctx *ctx, const float *grad_u_new_d, float *grad_params_d) {
     if (!ctx) return MPPI_ERR_INVALID_ARG;
-    (void)grad_u_new_d;
-    (void)grad_params_d;
-    return fail(ctx, MPPI_ERR_UNSUPPORTED, "backward is not available for this context");
+    if (!ctx->differentiable)
+        return fail(ctx, MPPI_ERR_UNSUPPORTED,
+                    "backward needs CARTPOLE dynamics, QUADRATIC cost and EULER");
+    if (!ctx->have_step) return fail(ctx, MPPI_ERR_UNSUPPORTED, "backward needs a prior mppi_step");
+    if (!grad_u_new_d || !grad_params_d)
+        return fail(ctx, MPPI_ERR_INVALID_ARG, "grad_u_new and grad_params must be device pointers");
+    cudaError_t e;
+    const size_t need = mppi::adjoint_scratch_floats(ctx->K, ctx->T);
+    if (ctx->scr.adj_floats < need) {
+        if (ctx->scr.adj) cudaFree(ctx->scr.adj);
+        ctx->scr.adj = nullptr;
+        ctx->scr.adj_floats = 0;
+        if ((e = dalloc(&ctx->scr.adj, need)) != cudaSuccess)
+            return cuda_fail(ctx, e, "adjoint scratch allocation");
+        ctx->scr.adj_floats = need;
+    }
+    StepParams p = make_params(*ctx);
+    {
+        ProfScope ps(ctx, MPPI_PROF_ADJOINT);
+        e = mppi::launch_adjoint(*ctx, p, grad_u_new_d, ctx->scr.saved_in,
+                                 ctx->scr.saved_in + ctx->nx, ctx->scr.adj, grad_params_d,
+                                 ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
+    return MPPI_OK;
 }
 
 mppi_status mppi_get_counter(mppi_ctx *ctx, uint64_t *counter) {

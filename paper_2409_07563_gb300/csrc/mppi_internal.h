@@ -36,6 +36,9 @@ struct Scratch {
     float *grad_partials = nullptr;     // adjoint block partials
     size_t grad_partials_floats = 0;
     float *io = nullptr;                // staging for mppi_step_host: x0, u_nom, u_new, stats
+    float *saved_in = nullptr;          // x0 and u_nom of the latest step (differentiable contexts)
+    float *adj = nullptr;               // adjoint scratch (allocated by the first backward)
+    size_t adj_floats = 0;
 };
 
 // Everything a rollout / update launch needs, passed by value.
@@ -50,6 +53,7 @@ struct StepParams {
     int n_dyn_params, n_cost_params, map_h, map_w;
     // scratch
     float *S, *partials, *upartials, *scalars;
+    float *saved_in;                    // non-null: block 0 of the rollout copies x0, u_nom here
     unsigned int *tickets, *status;
     unsigned long long *counter, *last_step;
 };
@@ -89,6 +93,7 @@ struct mppi_ctx {
     cudaStream_t stream = nullptr;
     int device = 0, num_sms = 0;
     bool have_step = false;
+    bool differentiable = false;        // cart-pole + quadratic + Euler
     std::string err;
     ProfileRecord prof;
 };
@@ -104,6 +109,11 @@ cudaError_t launch_update(const mppi_ctx &c, const StepParams &p);
 cudaError_t launch_sample_noise(uint64_t seed, uint64_t step, int K, int Q, uint32_t *bits,
                                 float *z, cudaStream_t s);
 cudaError_t launch_store_u64(unsigned long long *dst, unsigned long long v, cudaStream_t s);
+// adjoint.cu: backward of the cart-pole step
+size_t adjoint_scratch_floats(int K, int T);
+cudaError_t launch_adjoint(const mppi_ctx &c, const StepParams &sp, const float *G,
+                           const float *x0, const float *u_nom, float *scratch,
+                           float *grad_out, cudaStream_t s);
 // rollout_quad.cu: four lanes per quadrotor sample
 bool quad_group_applicable(const mppi_ctx &c);
 size_t quad_group_smem_bytes(const mppi_ctx &c);

@@ -46,6 +46,10 @@ __global__ void __launch_bounds__(256) rollout_kernel(const StepParams p) {
     Cost::prepare(p.cost_params, s_cost, tid, nt);
     __syncthreads();
 
+    if (p.saved_in && blockIdx.x == 0) {  // inputs kept for a later backward
+        for (int i = tid; i < NX; i += nt) p.saved_in[i] = p.x0[i];
+        for (int i = tid; i < p.T * NU; i += nt) p.saved_in[NX + i] = s_u[i];
+    }
     const NoiseKey nk = make_noise_key(p.seed, *p.counter);
     const CostCtx cc{p.map, p.map_h, p.map_w};
     float sig[NU], ivar[NU];
