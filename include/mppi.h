@@ -46,6 +46,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define MPPI_API __attribute__((visibility("default")))
+#else
+#define MPPI_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -144,7 +150,7 @@ typedef struct {
 } mppi_options;
 
 /* Fills *opt with the defaults (beta 1, FP32, seed 0, automatic launch). */
-void mppi_default_options(mppi_options *opt);
+MPPI_API void mppi_default_options(mppi_options *opt);
 
 /* Creates a context for K samples over horizon T with step dt, temperature
  * lambda > 0 and per-channel noise standard deviations sigma[nu] (host,
@@ -152,16 +158,16 @@ void mppi_default_options(mppi_options *opt);
  * scratch (costs, partial sums, counters; O(K + T nu) floats) and a device
  * copy of the parameters and map.  opt may be NULL (defaults).  Limits:
  * 1 <= K <= 2^24, 1 <= T, T * nu <= 16384.  On error *out is NULL. */
-mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cost,
+MPPI_API mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cost,
                         int K, int T, float dt, float lambda, const float *sigma,
                         const mppi_options *opt, mppi_ctx **out);
 
 /* Frees the context and its device memory (synchronises its stream). */
-void mppi_destroy(mppi_ctx *ctx);
+MPPI_API void mppi_destroy(mppi_ctx *ctx);
 
 /* Sets the CUDA stream (a cudaStream_t, e.g. torch's current stream) on which
  * the context enqueues its work.  NULL selects the legacy default stream. */
-mppi_status mppi_set_stream(mppi_ctx *ctx, void *cuda_stream);
+MPPI_API mppi_status mppi_set_stream(mppi_ctx *ctx, void *cuda_stream);
 
 /* One MPPI iteration (Algorithm 1 with I = 1), asynchronous on the stream.
  *   x0_d      [nx]     initial state
@@ -172,20 +178,20 @@ mppi_status mppi_set_stream(mppi_ctx *ctx, void *cuda_stream);
  *   costs_d   [K]      out: S_k, or NULL
  * If no sample cost is finite, u_new = u_nom, w = 0, F = rho = +inf and the
  * device status word records MPPI_ERR_NUMERIC (see mppi_poll_status). */
-mppi_status mppi_step(mppi_ctx *ctx, const float *x0_d, const float *u_nom_d,
+MPPI_API mppi_status mppi_step(mppi_ctx *ctx, const float *x0_d, const float *u_nom_d,
                       float *u_new_d, float *weights_d, float *stats_d, float *costs_d);
 
 /* Same iteration from HOST buffers: copies x0_h and u_nom_h to the device,
  * runs mppi_step, copies u_new_h [T*nu] (and stats_h [4] unless NULL) back and
  * synchronises the stream before returning.  Pinned host memory gives
  * asynchronous copies; pageable memory works too. */
-mppi_status mppi_step_host(mppi_ctx *ctx, const float *x0_h, const float *u_nom_h,
+MPPI_API mppi_status mppi_step_host(mppi_ctx *ctx, const float *x0_h, const float *u_nom_h,
                            float *u_new_h, float *stats_h);
 
 /* Replaces the dynamics and/or cost parameter arrays (host, same lengths as at
  * create; NULL keeps the current one).  Synchronises the stream, then copies;
  * later steps use the new values. */
-mppi_status mppi_set_params(mppi_ctx *ctx, const float *dyn_params, const float *cost_params);
+MPPI_API mppi_status mppi_set_params(mppi_ctx *ctx, const float *dyn_params, const float *cost_params);
 
 /* Gradient of L = sum_{t,j} grad_u_new[t,j] u_new[t,j] of the most recent
  * mppi_step with respect to theta = (Q[0..3], R, l, m_cart) at fixed noise
@@ -195,21 +201,21 @@ mppi_status mppi_set_params(mppi_ctx *ctx, const float *dyn_params, const float 
  * from checkpoints stored every ceil(sqrt(T)) steps.
  *   grad_u_new_d [T*nu] (device), grad_params_d [7] (device, overwritten).
  * Needs a prior mppi_step on this context; MPPI_ERR_UNSUPPORTED otherwise. */
-mppi_status mppi_step_backward(mppi_ctx *ctx, const float *grad_u_new_d,
+MPPI_API mppi_status mppi_step_backward(mppi_ctx *ctx, const float *grad_u_new_d,
                                float *grad_params_d);
 
 /* Step counter used as the noise counter's high words.  get synchronises the
  * stream (the counter lives on the device); set is ordered on the stream. */
-mppi_status mppi_get_counter(mppi_ctx *ctx, uint64_t *counter);
-mppi_status mppi_set_counter(mppi_ctx *ctx, uint64_t counter);
+MPPI_API mppi_status mppi_get_counter(mppi_ctx *ctx, uint64_t *counter);
+MPPI_API mppi_status mppi_set_counter(mppi_ctx *ctx, uint64_t counter);
 
 /* Synchronises the stream, reads and clears the device status word:
  * MPPI_OK, or the first device-side condition recorded since the last poll. */
-mppi_status mppi_poll_status(mppi_ctx *ctx);
+MPPI_API mppi_status mppi_poll_status(mppi_ctx *ctx);
 
 /* Message of the last error on this context ("" if none); valid until the
  * next call on the context. */
-const char *mppi_last_error(const mppi_ctx *ctx);
+MPPI_API const char *mppi_last_error(const mppi_ctx *ctx);
 
 /* Per-kernel timing with CUDA events recorded on the context's stream around
  * every launch the context makes while profiling is on.  mppi_profile(ctx, 1)
@@ -219,15 +225,56 @@ const char *mppi_last_error(const mppi_ctx *ctx);
  * elapsed milliseconds and the number of launches (arrays of
  * MPPI_PROF_SLOTS entries; either may be NULL). */
 enum { MPPI_PROF_ROLLOUT = 0, MPPI_PROF_UPDATE = 1, MPPI_PROF_ADJOINT = 2, MPPI_PROF_SLOTS = 4 };
-mppi_status mppi_profile(mppi_ctx *ctx, int enable);
-mppi_status mppi_profile_read(mppi_ctx *ctx, float *ms, int *launches);
+MPPI_API mppi_status mppi_profile(mppi_ctx *ctx, int enable);
+MPPI_API mppi_status mppi_profile_read(mppi_ctx *ctx, float *ms, int *launches);
 
 /* Diagnostic: the raw Philox words and standard normals the kernels use, for
  * samples k < K and blocks q < Q at (seed, step): bits_d [K*Q*4] (uint32) and
  * z_d [K*Q*4] (float), either may be NULL; element (k, q, lane) at
  * ((k * Q) + q) * 4 + lane.  Enqueued on `cuda_stream`. */
-mppi_status mppi_sample_noise(uint64_t seed, uint64_t step, int K, int Q,
+MPPI_API mppi_status mppi_sample_noise(uint64_t seed, uint64_t step, int K, int Q,
                               uint32_t *bits_d, float *z_d, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched MPPI: many independent instances of uneven K and T stepped by one
+ * persistent launch pair replayed from a CUDA graph.  Algorithm 1 per
+ * instance, exactly as mppi_step (same noise definition with the instance's
+ * own seed and step counter, which starts at 0 and advances by one per
+ * mppi_batch_step).  Supported instances: CARTPOLE + QUADRATIC + EULER and
+ * QUADROTOR + QUADRATIC or QUAD_OBSTACLES (at most 32 spheres) + RK4.
+ * The device buffers named in the descriptors are fixed at creation (the
+ * graph refers to them) and must outlive the batch.  mppi_batch_create picks
+ * the block size by timing 64/128/256-thread candidates on the device unless
+ * opt->block_threads gives one (the result is cached per workload in the
+ * process); it synchronises the device.  opt->beta is not used (each
+ * descriptor carries its own). */
+typedef struct mppi_batch mppi_batch;
+
+typedef struct {
+    mppi_dynamics_desc dyn;
+    mppi_cost_desc cost;
+    int K, T;
+    float dt, lambda;
+    const float *sigma;       /* host, nu */
+    uint64_t seed;            /* this instance's Philox key */
+    int beta;                 /* importance-sampling term of this instance: 1 or 0 */
+    const float *x0_d;        /* device, nx */
+    const float *u_nom_d;     /* device, T*nu */
+    float *u_new_d;           /* device, T*nu (may alias u_nom_d) */
+    float *stats_d;           /* device, 4 = [F, rho, eta, ess], or NULL */
+} mppi_instance_desc;
+
+MPPI_API mppi_status mppi_batch_create(int n, const mppi_instance_desc *desc, const mppi_options *opt,
+                              mppi_batch **out);
+/* One MPPI iteration of every instance, enqueued on cuda_stream. */
+MPPI_API mppi_status mppi_batch_step(mppi_batch *b, void *cuda_stream);
+/* Milliseconds from the start of the latest batch step to the completion of
+ * each instance's update (device %globaltimer stamps), ms [n].  Synchronises
+ * cuda_stream. */
+MPPI_API mppi_status mppi_batch_latency(mppi_batch *b, void *cuda_stream, float *ms);
+/* info[4] = block threads, rollout grid, rollout work items, update work items. */
+MPPI_API mppi_status mppi_batch_info(const mppi_batch *b, int *info);
+MPPI_API void mppi_batch_destroy(mppi_batch *b);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free weighting and update.  The paper has no counterpart: this
@@ -254,7 +301,7 @@ mppi_status mppi_sample_noise(uint64_t seed, uint64_t step, int K, int Q,
  * race: order them on one stream. */
 #define MPPI_NOALLOC_MAX_K 65536
 #define MPPI_NOALLOC_MAX_TNU 4096
-mppi_status mppi_update_noalloc(const float *costs_d, int K, int T, int nu, float lambda,
+MPPI_API mppi_status mppi_update_noalloc(const float *costs_d, int K, int T, int nu, float lambda,
                                 const float *sigma_h, uint64_t seed, uint64_t step,
                                 const float *u_nom_d, float *u_new_d, float *weights_d,
                                 float *stats_d, void *cuda_stream);

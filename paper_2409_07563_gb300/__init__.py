@@ -313,3 +313,90 @@ def _make_step_function():
             return g, None, None, None
 
     return _Step
+
+
+# ---------------------------------------------------------------------------
+# batched instances (mppi_batch_*)
+# ---------------------------------------------------------------------------
+class MPPIBatch:
+    """Many independent MPPI instances stepped by one graph launch.
+
+    ``problems`` are problem dictionaries (``workloads.py``); the batch owns
+    one device buffer each for all x0, u_nom, u_new and statistics (slices
+    per instance), created from the problems' x0 / u_nom.
+    """
+
+    def __init__(self, problems, block_threads=0, device="cuda"):
+        import torch
+        from ._lib import InstanceDesc
+        L = load()
+        self.n = len(problems)
+        self.problems = problems
+        self._keep = []
+        nx = [int(p["nx"]) for p in problems]
+        tn = [int(p["T"]) * int(p["nu"]) for p in problems]
+        self.x0 = torch.tensor(np.concatenate([np.asarray(p["x0"], np.float32) for p in problems]),
+                               device=device)
+        self.u_nom = torch.tensor(np.concatenate(
+            [np.asarray(p["u_nom"], np.float32).reshape(-1) for p in problems]), device=device)
+        self.u_new = torch.zeros_like(self.u_nom)
+        self.stats = torch.zeros(4 * self.n, device=device)
+        self._xo = np.concatenate([[0], np.cumsum(nx)]).astype(int)
+        self._uo = np.concatenate([[0], np.cumsum(tn)]).astype(int)
+        descs = (InstanceDesc * self.n)()
+        for i, p in enumerate(problems):
+            dyn = _f32(p["dyn_params"])
+            cost = _f32(p["cost_params"])
+            sig = _f32(p["sigma"])
+            self._keep += [dyn, cost, sig]
+            d = descs[i]
+            d.dyn = DynamicsDesc(int(p["dyn_kind"]), int(p["integrator"]), int(p["nx"]),
+                                 int(p["nu"]), _fptr(dyn), dyn.size)
+            d.cost = CostDesc(int(p["cost_kind"]), _fptr(cost), cost.size, None, 0, 0)
+            d.K, d.T = int(p["K"]), int(p["T"])
+            d.dt, d.lambda_ = float(p["dt"]), float(p["lam"])
+            d.sigma = _fptr(sig)
+            d.seed = int(p["seed"]) & (2**64 - 1)
+            d.beta = int(p["beta"])
+            d.x0_d = self.x0.data_ptr() + 4 * int(self._xo[i])
+            d.u_nom_d = self.u_nom.data_ptr() + 4 * int(self._uo[i])
+            d.u_new_d = self.u_new.data_ptr() + 4 * int(self._uo[i])
+            d.stats_d = self.stats.data_ptr() + 16 * i
+        opt = Options()
+        L.mppi_default_options(ctypes.byref(opt))
+        opt.block_threads = int(block_threads)
+        h = ctypes.c_void_p()
+        check(L.mppi_batch_create(self.n, descs, ctypes.byref(opt), ctypes.byref(h)),
+              "mppi_batch_create")
+        self._h = h
+
+    def step(self, stream=None):
+        check(load().mppi_batch_step(self._h, _stream_handle(stream)), "mppi_batch_step")
+
+    def latency_ms(self, stream=None):
+        out = (ctypes.c_float * self.n)()
+        check(load().mppi_batch_latency(self._h, _stream_handle(stream), out), "mppi_batch_latency")
+        return np.array(out[:], dtype=np.float64)
+
+    def info(self):
+        out = (ctypes.c_int * 4)()
+        check(load().mppi_batch_info(self._h, out), "mppi_batch_info")
+        return dict(block_threads=out[0], grid=out[1], rollout_items=out[2], update_items=out[3])
+
+    def u_new_of(self, i):
+        p = self.problems[i]
+        return self.u_new[self._uo[i]:self._uo[i + 1]].view(int(p["T"]), int(p["nu"]))
+
+    def stats_of(self, i):
+        return self.stats[4 * i:4 * i + 4]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mppi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

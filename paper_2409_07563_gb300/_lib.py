@@ -51,7 +51,8 @@ class Options(ctypes.Structure):
 class InstanceDesc(ctypes.Structure):
     _fields_ = [("dyn", DynamicsDesc), ("cost", CostDesc), ("K", ctypes.c_int), ("T", ctypes.c_int),
                 ("dt", ctypes.c_float), ("lambda_", ctypes.c_float), ("sigma", c_float_p),
-                ("seed", ctypes.c_uint64), ("x0", c_float_p), ("u_nom", c_float_p)]
+                ("seed", ctypes.c_uint64), ("beta", ctypes.c_int), ("x0_d", ctypes.c_void_p), ("u_nom_d", ctypes.c_void_p),
+                ("u_new_d", ctypes.c_void_p), ("stats_d", ctypes.c_void_p)]
 
 
 _lib = None
@@ -111,6 +112,10 @@ def _optional(L):
         L.mppi_batch_create.restype = ctypes.c_int
         L.mppi_batch_step.argtypes = [vp, vp]
         L.mppi_batch_step.restype = ctypes.c_int
+        L.mppi_batch_latency.argtypes = [vp, vp, c_float_p]
+        L.mppi_batch_latency.restype = ctypes.c_int
+        L.mppi_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        L.mppi_batch_info.restype = ctypes.c_int
         L.mppi_batch_destroy.argtypes = [vp]
         L.mppi_batch_destroy.restype = None
 

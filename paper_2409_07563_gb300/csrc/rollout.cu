@@ -14,6 +14,7 @@
 #include "models.cuh"
 #include "mppi_internal.h"
 #include "rollout_tail.cuh"
+#include "sample_rollout.cuh"
 
 namespace mppi {
 namespace {
@@ -50,57 +51,12 @@ __global__ void __launch_bounds__(256) rollout_kernel(const StepParams p) {
         for (int i = tid; i < NX; i += nt) p.saved_in[i] = p.x0[i];
         for (int i = tid; i < p.T * NU; i += nt) p.saved_in[NX + i] = s_u[i];
     }
-    const NoiseKey nk = make_noise_key(p.seed, *p.counter);
-    const CostCtx cc{p.map, p.map_h, p.map_w};
-    float sig[NU], ivar[NU];
-#pragma unroll
-    for (int j = 0; j < NU; ++j) {
-        sig[j] = p.sigma[j];
-        ivar[j] = p.ivar[j];
-    }
-
+    const SampleArgs args{p.T, p.dt, p.lam_beta, p.sigma, p.ivar, p.x0, s_u, s_dyn, s_cost,
+                          CostCtx{p.map, p.map_h, p.map_w}, make_noise_key(p.seed, *p.counter)};
     const int k = blockIdx.x * nt + tid;
     float S = __int_as_float(0x7f800000);  // inactive lanes take no part
     if (k < p.K) {
-        float x[NX];
-#pragma unroll
-        for (int i = 0; i < NX; ++i) x[i] = p.x0[i];
-        CompSum J;
-        const int QT = (p.T + 3) / 4;
-        // the next group's normals are drawn while this group integrates
-        // (software pipelining keeps Philox + Box-Muller off the state chain);
-        // the block drawn after the last group is never used
-        float z[4 * NU];
-        group_normals<NU>(nk, static_cast<uint32_t>(k), 0, QT, z);
-        for (int t0 = 0; t0 < p.T; t0 += 4) {
-            float zn[4 * NU];
-            if (Dyn::kPipelineNoise)
-                group_normals<NU>(nk, static_cast<uint32_t>(k), t0 + 4, QT, zn);
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                const int t = t0 + s;
-                if (t < p.T) {
-                    float v[NU];
-                    float is = 0.f;
-#pragma unroll
-                    for (int j = 0; j < NU; ++j) {
-                        const float u = s_u[t * NU + j];
-                        v[j] = u + sig[j] * z[4 * j + s];
-                        is += (v[j] - 0.5f * u) * (u * ivar[j]);
-                    }
-                    Dyn::step(x, v, s_dyn, p.dt);
-                    J.add(Cost::running(x, v, s_cost, cc) + p.lam_beta * is);
-                }
-            }
-            if (Dyn::kPipelineNoise) {
-#pragma unroll
-                for (int i = 0; i < 4 * NU; ++i) z[i] = zn[i];
-            } else if (t0 + 4 < p.T) {
-                group_normals<NU>(nk, static_cast<uint32_t>(k), t0 + 4, QT, z);
-            }
-        }
-        J.add(Cost::terminal(x, s_cost, cc));
-        S = J.value();
+        S = generic_sample_cost<Dyn, Cost>(args, static_cast<uint32_t>(k));
         p.S[k] = S;
     }
 

@@ -1,0 +1,72 @@
+// sample_rollout.cuh -- the per-sample rollout of steps a1-a3 for one thread
+// (Algorithm 1 inner loop): noise from the counter, x <- F(x, u + eps),
+// J += l(x, v) - lambda I(v) with a compensated sum, J += phi(x) at the end.
+// Shared by the single-instance and the batched rollout kernels.
+#pragma once
+
+#include "device_common.cuh"
+#include "models.cuh"
+
+namespace mppi {
+
+struct SampleArgs {
+    int T;
+    float dt, lam_beta;
+    const float *sigma, *ivar;  // nu entries each
+    const float *x0;            // nx, global
+    const float *s_u;           // T*nu nominal controls, shared memory
+    const float *s_dyn, *s_cost;
+    CostCtx cc;
+    NoiseKey nk;
+};
+
+template <class Dyn, class Cost>
+__device__ __forceinline__ float generic_sample_cost(const SampleArgs &a, uint32_t k) {
+    constexpr int NX = Dyn::NX, NU = Dyn::NU;
+    float sig[NU], ivar[NU];
+#pragma unroll
+    for (int j = 0; j < NU; ++j) {
+        sig[j] = a.sigma[j];
+        ivar[j] = a.ivar[j];
+    }
+    float x[NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) x[i] = a.x0[i];
+    CompSum J;
+    const int T = a.T, QT = (T + 3) / 4;
+    // the next group's normals are drawn while this group integrates
+    // (software pipelining keeps Philox + Box-Muller off the state chain);
+    // the block drawn after the last group is never used
+    float z[4 * NU];
+    group_normals<NU>(a.nk, k, 0, QT, z);
+    for (int t0 = 0; t0 < T; t0 += 4) {
+        float zn[4 * NU];
+        if (Dyn::kPipelineNoise) group_normals<NU>(a.nk, k, t0 + 4, QT, zn);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int t = t0 + s;
+            if (t < T) {
+                float v[NU];
+                float is = 0.f;
+#pragma unroll
+                for (int j = 0; j < NU; ++j) {
+                    const float u = a.s_u[t * NU + j];
+                    v[j] = u + sig[j] * z[4 * j + s];
+                    is += (v[j] - 0.5f * u) * (u * ivar[j]);
+                }
+                Dyn::step(x, v, a.s_dyn, a.dt);
+                J.add(Cost::running(x, v, a.s_cost, a.cc) + a.lam_beta * is);
+            }
+        }
+        if (Dyn::kPipelineNoise) {
+#pragma unroll
+            for (int i = 0; i < 4 * NU; ++i) z[i] = zn[i];
+        } else if (t0 + 4 < T) {
+            group_normals<NU>(a.nk, k, t0 + 4, QT, z);
+        }
+    }
+    J.add(Cost::terminal(x, a.s_cost, a.cc));
+    return J.value();
+}
+
+}  // namespace mppi
