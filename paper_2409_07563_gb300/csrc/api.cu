@@ -97,11 +97,15 @@ void free_ctx(mppi_ctx *c) {
 void plan_launch(mppi_ctx &c) {
     mppi::LaunchPlan &pl = c.plan;
     const bool group = mppi::quad_group_applicable(c) && c.variant_opt != mppi::kVariantGeneric;
-    pl.variant = group ? mppi::kVariantQuadGroup : mppi::kVariantGeneric;
+    const bool mlp_tc = c.precision == MPPI_PREC_BF16_MLP;
+    pl.variant = mlp_tc ? mppi::kVariantMlpBf16
+                        : group ? mppi::kVariantQuadGroup : mppi::kVariantGeneric;
     const int lanes = group ? 4 : 1;             // threads per sample
     const long threads_needed = static_cast<long>(c.K) * lanes;
     if (c.block_threads > 0) {
         pl.rollout_threads = c.block_threads;
+    } else if (mlp_tc) {
+        pl.rollout_threads = 64;                 // two warps of 32 samples
     } else if (group) {
         pl.rollout_threads = 64;
     } else {
@@ -250,7 +254,10 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     mppi_status st = validate_cost(*dyn, *cost, nx, nu, msg);
     if (st != MPPI_OK) return st;
     if (!mppi::rollout_supported(dyn->kind, cost->kind, nx, nu)) return MPPI_ERR_UNSUPPORTED;
-    if (o.precision != MPPI_PREC_FP32) return MPPI_ERR_UNSUPPORTED;
+    if (o.precision != MPPI_PREC_FP32 &&
+        !(o.precision == MPPI_PREC_BF16_MLP && dyn->kind == MPPI_DYN_BICYCLE_MLP &&
+          cost->kind == MPPI_COST_COSTMAP_SPEED))
+        return MPPI_ERR_UNSUPPORTED;
 
     mppi_ctx *c = new (std::nothrow) mppi_ctx;
     if (!c) return MPPI_ERR_OOM;
@@ -324,9 +331,10 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
         free_ctx(c);
         return MPPI_ERR_CUDA;
     }
-    c->plan.rollout_smem = c->plan.variant == mppi::kVariantQuadGroup
-                               ? mppi::quad_group_smem_bytes(*c)
-                               : mppi::rollout_smem_bytes(*c);
+    c->plan.rollout_smem =
+        c->plan.variant == mppi::kVariantQuadGroup ? mppi::quad_group_smem_bytes(*c)
+        : c->plan.variant == mppi::kVariantMlpBf16 ? mppi::mlp_bf16_smem_bytes(*c, c->plan.rollout_threads)
+                                                   : mppi::rollout_smem_bytes(*c);
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     if (c->plan.rollout_smem > static_cast<size_t>(max_smem)) {
@@ -334,7 +342,8 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
         return MPPI_ERR_UNSUPPORTED;
     }
     if ((e = mppi::rollout_prepare(*c)) != cudaSuccess ||
-        (c->plan.variant == mppi::kVariantQuadGroup && (e = mppi::quad_group_prepare(*c)) != cudaSuccess)) {
+        (c->plan.variant == mppi::kVariantQuadGroup && (e = mppi::quad_group_prepare(*c)) != cudaSuccess) ||
+        (c->plan.variant == mppi::kVariantMlpBf16 && (e = mppi::mlp_bf16_prepare(*c)) != cudaSuccess)) {
         free_ctx(c);
         return MPPI_ERR_CUDA;
     }
@@ -370,6 +379,7 @@ mppi_status mppi_step(mppi_ctx *ctx, const float *x0_d, const float *u_nom_d, fl
     {
         ProfScope ps(ctx, MPPI_PROF_ROLLOUT);
         e = ctx->plan.variant == mppi::kVariantQuadGroup ? mppi::launch_quad_group(*ctx, p)
+            : ctx->plan.variant == mppi::kVariantMlpBf16 ? mppi::launch_mlp_bf16(*ctx, p)
                                                          : mppi::launch_rollout(*ctx, p);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rollout launch");

@@ -58,7 +58,7 @@ struct StepParams {
     unsigned long long *counter, *last_step;
 };
 
-enum RolloutVariant { kVariantGeneric = 1, kVariantQuadGroup = 2 };
+enum RolloutVariant { kVariantGeneric = 1, kVariantQuadGroup = 2, kVariantMlpBf16 = 3 };
 
 struct LaunchPlan {
     int variant = kVariantGeneric;
@@ -119,5 +119,9 @@ bool quad_group_applicable(const mppi_ctx &c);
 size_t quad_group_smem_bytes(const mppi_ctx &c);
 cudaError_t quad_group_prepare(const mppi_ctx &c);
 cudaError_t launch_quad_group(const mppi_ctx &c, const StepParams &p);
+// rollout_mlp_bf16.cu: bicycle + MLP on the tensor cores
+size_t mlp_bf16_smem_bytes(const mppi_ctx &c, int threads);
+cudaError_t mlp_bf16_prepare(const mppi_ctx &c);
+cudaError_t launch_mlp_bf16(const mppi_ctx &c, const StepParams &p);
 
 }  // namespace mppi

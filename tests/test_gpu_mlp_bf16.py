@@ -1,0 +1,69 @@
+"""BF16 tensor-core MLP path (precision MPPI_PREC_BF16_MLP) against the FP64
+oracle.  BF16 operands round the MLP inputs, weights and activations to 8
+significant bits, so this path has no 1e-4 sigma bound; what is checked:
+
+  * per-sample trajectory costs: median relative error <= 1e-3, 99th
+    percentile <= 1e-2 (BF16 rounding of a residual that is ~10% of the
+    dynamics, integrated over the horizon);
+  * stage-isolated weighting and update from the GPU's own costs exactly as
+    for the FP32 path (those stages are FP32);
+  * end to end with spread weights (lambda = 100): |du| <= 0.05 sigma.
+The measured errors are printed for the parity report.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from _util import as_f32_problem, n_threads
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def m():
+    if not torch.cuda.is_available():
+        pytest.fail("the -m gpu tests need a CUDA GPU")
+    import paper_2409_07563_gb300 as mod
+    mod.build()
+    return mod
+
+
+def run(m, p, precision):
+    ctl = m.MPPI.from_problem(p, precision=precision)
+    x0 = torch.tensor(p["x0"], dtype=torch.float32, device="cuda")
+    u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device="cuda")
+    out = ctl.step(x0, u, want_weights=True, want_costs=True)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy().astype(np.float64) for k, v in out.items()}
+
+
+@pytest.mark.parametrize("K,T,lam", [(16384, 100, 1.0), (2001, 21, 5.0), (4096, 100, 100.0)])
+def test_bf16_mlp_costs_and_update(m, K, T, lam):
+    p = as_f32_problem(W.bicycle_mlp(K=K, T=T, lam=lam))
+    g = run(m, p, m.MPPI_PREC_BF16_MLP)
+    o = oracle.mppi_step(p, n_threads=n_threads(), want_eps=True)
+    rel = np.abs(g["costs"] - o["S"]) / np.maximum(1.0, np.abs(o["S"]))
+    print(f"\nBF16 MLP K={K} T={T} lam={lam}: S rel err median {np.median(rel):.2e} "
+          f"p99 {np.percentile(rel, 99):.2e} max {rel.max():.2e}")
+    assert np.median(rel) <= 1e-3
+    assert np.percentile(rel, 99) <= 1e-2
+    # weighting and update stages from the GPU's own costs (FP32 stages)
+    w_ref, st_ref, _ = oracle.weights(g["costs"], lam)
+    x = (g["costs"] - st_ref[1]) / lam
+    assert np.all(np.abs(g["weights"] - w_ref) <= 2e-5 * (1 + np.abs(x)) * w_ref + 1e-9)
+    u_iso = p["u_nom"] + np.einsum("k,ktj->tj", w_ref, o["eps"])
+    assert np.all(np.abs(g["u_new"] - u_iso) <= 1e-5 * p["sigma"][None, :])
+    err = np.abs(g["u_new"] - o["u_new"]) / p["sigma"][None, :]
+    print(f"BF16 MLP end-to-end max |du|/sigma = {err.max():.3e}, ESS = {o['stats'][3]:.2f}")
+    if lam >= 100:
+        assert err.max() <= 0.05
+
+
+def test_bf16_and_fp32_paths_agree_on_costs(m):
+    p = as_f32_problem(W.bicycle_mlp(K=1024, T=60, lam=10.0))
+    g16 = run(m, p, m.MPPI_PREC_BF16_MLP)
+    g32 = run(m, p, m.MPPI_PREC_FP32)
+    rel = np.abs(g16["costs"] - g32["costs"]) / np.maximum(1.0, np.abs(g32["costs"]))
+    assert np.median(rel) <= 1e-3
