@@ -207,6 +207,90 @@ def make_workload(name, K=None):
     raise ValueError(name)
 
 
+def kernel_source_hash():
+    """Hash of the CUDA sources; a stored ncu traffic figure is only used while
+    the kernels are unchanged since it was taken."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2409_07563_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def time_steps(fn, steps, warmup=3):
+    """Mean milliseconds of fn() over `steps` calls (CUDA events, current stream)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(steps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / steps
+
+
+def extensions(m, dev):
+    """The batched, differentiable and BF16-MLP forms on the same GPU."""
+    import torch
+    out = {}
+    # batched: 256 instances, cart-pole and quadrotor, uneven K and T
+    probs = W.batched()
+    b = m.MPPIBatch(probs)
+    ms = time_steps(b.step, 20)
+    lat = b.latency_ms()
+    rs = sum(p["K"] * p["T"] for p in probs)
+    out["batched"] = {"workload": "256 instances (128 cart-pole, 128 quadrotor), K in "
+                                  "{256..8192}, T in {50..200}, one graph launch per step",
+                      "rollout_steps_per_s": rs / (ms * 1e-3), "ms_per_step": ms,
+                      "instance_latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                              "p99": float(np.percentile(lat, 99))},
+                      "block_threads": b.info()["block_threads"]}
+    b.close()
+    # differentiable: cart-pole K=4096, T=100, forward + adjoint backward
+    p = W.differentiable()
+    ctl = m.MPPI.from_problem(p)
+    x0 = torch.tensor(p["x0"], dtype=torch.float32, device=dev)
+    u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device=dev)
+    tgt = torch.tensor(p["u_target"].reshape(-1), dtype=torch.float32, device=dev)
+    un = torch.empty_like(u)
+    gbuf = torch.empty_like(u)
+
+    def fwd_bwd():
+        ctl.step_into(x0, u, un)
+        torch.mul(torch.sub(un, tgt), 2.0, out=gbuf)
+        ctl.backward(gbuf)
+    ms_f = time_steps(lambda: ctl.step_into(x0, u, un), 20)
+    ms_fb = time_steps(fwd_bwd, 20)
+    out["differentiable"] = {"workload": "cart-pole K=4096 T=100, loss ||u_new - u_target||^2, "
+                                         "grads w.r.t. Q(4), R, l, m_c",
+                             "forward_ms": ms_f, "forward_backward_ms": ms_fb,
+                             "rollout_steps_per_s": p["K"] * p["T"] / (ms_fb * 1e-3)}
+    ctl.close()
+    # precision: bicycle + MLP, BF16 tensor cores vs FP32 CUDA cores
+    p = W.bicycle_mlp()
+    x0 = torch.tensor(p["x0"], dtype=torch.float32, device=dev)
+    u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device=dev)
+    un = torch.empty_like(u)
+    res = {}
+    for name, prec in (("bf16", m.MPPI_PREC_BF16_MLP), ("fp32", m.MPPI_PREC_FP32)):
+        c = m.MPPI.from_problem(p, precision=prec)
+        res[name] = time_steps(lambda: c.step_into(x0, u, un), 10)
+        c.close()
+    out["bf16_mlp"] = {"workload": "bicycle + MLP 6-64-64-4, K=16384 T=100, costmap 512x512",
+                       "ms_per_step": res["bf16"], "fp32_ms_per_step": res["fp32"],
+                       "rollout_steps_per_s": p["K"] * p["T"] / (res["bf16"] * 1e-3),
+                       "mlp_tflops": 2 * (6 * 64 + 64 * 64 + 64 * 4) * p["K"] * p["T"]
+                       / (res["bf16"] * 1e-3) / 1e12}
+    return out
+
+
 def workload_config(p):
     return {"workload": f"{p['name']} (lambda={p['lam']}, seeded inputs)",
             "K": p["K"], "T": p["T"], "nx": p["nx"], "nu": p["nu"],
@@ -220,6 +304,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extensions", action="store_true",
+                    help="skip the batched / differentiable / BF16 measurements")
     ap.add_argument("--K", type=int, default=None, help="override the sample count")
     ap.add_argument("--workload", default="quadrotor", choices=sorted(FLOPS_PER_ROLLOUT_STEP),
                     help="quadrotor (configuration 1, the headline) or a diagnostic run")
@@ -324,7 +410,9 @@ def main():
     if os.path.exists(traffic_file):
         try:
             with open(traffic_file) as f:
-                roofline["traffic"] = json.load(f).get("bytes_per_launch")
+                tr = json.load(f)
+            if tr.get("kernel_source_hash") == kernel_source_hash() and tr.get("K") == p["K"]:
+                roofline["traffic"] = tr.get("bytes_per_launch")
         except (OSError, ValueError):
             pass
 
@@ -344,6 +432,8 @@ def main():
         "roofline": roofline,
         "clocks": clk,
     }
+    if world == 1 and not args.no_extensions and args.workload == "quadrotor":
+        line["extensions"] = extensions(m, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
     print(json.dumps(line), flush=True)
