@@ -85,7 +85,8 @@ void free_ctx(mppi_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
-    void *ptrs[] = {c->d_dyn, c->d_cost, c->d_map, c->scr.S, c->scr.partials, c->scr.upartials,
+    void *ptrs[] = {c->d_dyn, c->d_cost, c->d_map, c->scr.S, c->scr.w, c->scr.nz, c->scr.cand,
+                    c->scr.partials, c->scr.upartials,
                     c->scr.scalars, c->scr.tickets, c->scr.status, c->scr.counter,
                     c->scr.last_step, c->scr.ckpt, c->scr.grad_partials, c->scr.io,
                     c->scr.saved_in, c->scr.adj};
@@ -122,7 +123,6 @@ void plan_launch(mppi_ctx &c) {
     const int want = (2 * c.num_sms + pl.update_qtiles - 1) / pl.update_qtiles;
     pl.update_chunks = std::max(1, std::min(max_chunks, want));
     pl.update_chunk_len = (c.K + pl.update_chunks - 1) / pl.update_chunks;
-    pl.update_chunks = (c.K + pl.update_chunk_len - 1) / pl.update_chunk_len;
 }
 
 StepParams make_params(const mppi_ctx &c) {
@@ -148,6 +148,9 @@ StepParams make_params(const mppi_ctx &c) {
     p.map_h = c.map_h;
     p.map_w = c.map_w;
     p.S = c.scr.S;
+    p.w = c.scr.w;
+    p.nz = c.scr.nz;
+    p.cand = c.scr.cand;
     p.partials = c.scr.partials;
     p.upartials = c.scr.upartials;
     p.scalars = c.scr.scalars;
@@ -291,9 +294,13 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
 
     const int Q = nu * ((T + 3) / 4);
     const size_t max_blocks = (4 * static_cast<size_t>(K) + 31) / 32;  // 32-thread blocks, 4 lanes
+
     const size_t io_floats = static_cast<size_t>(nx) + 2 * static_cast<size_t>(T) * nu + 4;
     if ((e = dalloc(&c->scr.S, K)) != cudaSuccess ||
-        (e = dalloc(&c->scr.partials, 3 * max_blocks)) != cudaSuccess ||
+        (e = dalloc(&c->scr.w, K)) != cudaSuccess ||
+        (e = dalloc(&c->scr.nz, K)) != cudaSuccess ||
+        (e = dalloc(&c->scr.cand, 4 * static_cast<size_t>(K) + 256)) != cudaSuccess ||
+        (e = dalloc(&c->scr.partials, 4 * max_blocks)) != cudaSuccess ||
         (e = dalloc(&c->scr.upartials, static_cast<size_t>(mppi::kMaxUpdateChunks) * Q * 4)) != cudaSuccess ||
         (e = dalloc(&c->scr.scalars, 8)) != cudaSuccess ||
         (e = dalloc(&c->scr.tickets, 4)) != cudaSuccess ||
@@ -327,7 +334,8 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
         (e = cudaMemset(c->scr.status, 0, sizeof(unsigned int))) != cudaSuccess ||
         (e = cudaMemset(c->scr.counter, 0, sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMemset(c->scr.last_step, 0, sizeof(unsigned long long))) != cudaSuccess ||
-        (e = cudaMemset(c->scr.scalars, 0, 8 * sizeof(float))) != cudaSuccess) {
+        (e = cudaMemset(c->scr.scalars, 0, 7 * sizeof(float))) != cudaSuccess ||
+        (e = cudaMemset(c->scr.scalars + 7, 0xff, sizeof(float))) != cudaSuccess) {  // running min
         free_ctx(c);
         return MPPI_ERR_CUDA;
     }

@@ -24,9 +24,12 @@ constexpr int kMaxUpdateChunks = 64;  // split-K factor cap of the update
 // Device scratch owned by a context.
 struct Scratch {
     float *S = nullptr;                 // [K] trajectory costs
-    float *partials = nullptr;          // [3 * max rollout blocks] (rho_b, eta_b, eta2_b)
+    float *w = nullptr;                 // [K] weights of the listed samples (parallel to nz)
+    int *nz = nullptr;                  // [K] samples with non-zero weight, in index order
+    int *cand = nullptr;                // [4K] per-block weight candidates
+    float *partials = nullptr;          // [4 * max rollout blocks] (rho_b, eta_b, eta2_b, n_cand)
     float *upartials = nullptr;         // [kMaxUpdateChunks * Q * 4] update partial sums
-    float *scalars = nullptr;           // [8] rho, eta, F, ess, valid
+    float *scalars = nullptr;           // [8] rho, eta, F, ess, valid, nnz, update-done
     unsigned int *tickets = nullptr;    // [4] last-block tickets (self-resetting)
     unsigned int *status = nullptr;     // [1] device status word
     unsigned long long *counter = nullptr;    // [1] step counter
@@ -53,6 +56,8 @@ struct StepParams {
     int n_dyn_params, n_cost_params, map_h, map_w;
     // scratch
     float *S, *partials, *upartials, *scalars;
+    float *w;
+    int *nz, *cand;
     float *saved_in;                    // non-null: block 0 of the rollout copies x0, u_nom here
     unsigned int *tickets, *status;
     unsigned long long *counter, *last_step;
@@ -109,6 +114,10 @@ cudaError_t launch_update(const mppi_ctx &c, const StepParams &p);
 cudaError_t launch_sample_noise(uint64_t seed, uint64_t step, int K, int Q, uint32_t *bits,
                                 float *z, cudaStream_t s);
 cudaError_t launch_store_u64(unsigned long long *dst, unsigned long long v, cudaStream_t s);
+// launch configuration with programmatic dependent launch (kernels start with
+// a dependency wait, so consecutive step kernels overlap their launch)
+cudaLaunchConfig_t pdl_config(dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              cudaLaunchAttribute *attr);
 // adjoint.cu: backward of the cart-pole step
 size_t adjoint_scratch_floats(int K, int T);
 cudaError_t launch_adjoint(const mppi_ctx &c, const StepParams &sp, const float *G,

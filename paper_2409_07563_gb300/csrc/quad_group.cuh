@@ -134,13 +134,14 @@ struct QuadArgs {
     NoiseKey nk;
 };
 
-// Shared-memory copy of the cost: the quadratic block, c_crash at 32, and the
-// spheres as float4 (cx, cy, cz, -fl(r*r)) from kObsOff, padded to 32 with
-// spheres that are never hit.
+// Shared-memory copy of the cost: the quadratic block (0..30), c_crash at 31,
+// and the spheres as float4 (cx, cy, cz, -fl(r*r)) from kObsOff = 32, padded
+// to 32 spheres that are never hit.
 __device__ inline void quad_prepare_cost(const float *raw, bool obstacles, float *s_cost, int tid,
                                          int nt) {
     for (int i = tid; i < kQuadCostFloats; i += nt) s_cost[i] = raw[i];
-    if (tid == 0) s_cost[32] = obstacles ? raw[32] : 0.f;
+    if (tid == 0) s_cost[31] = obstacles ? raw[32] : 0.f;
+    static_assert(kObsOff >= kQuadCostFloats + 1, "c_crash slot overlaps the spheres");
     const int n = obstacles ? static_cast<int>(raw[31]) : 0;
     for (int i = tid; i < kMaxGroupObs; i += nt) {
         float4 o = make_float4(0.f, 0.f, 0.f, 3.0e38f);
@@ -166,7 +167,7 @@ __device__ __forceinline__ float quad_group_sample_cost(const QuadArgs &a, uint3
     const float dt = a.dt, h = 0.5f * dt, d6 = dt / 6.0f;
     const float sig = a.sigma[r], ivar = a.ivar[r], lamb = a.lam_beta;
     const float s_term = s_cost[30];
-    const float c_crash = kObstacles ? s_cost[32] : 0.f;
+    const float c_crash = kObstacles ? s_cost[31] : 0.f;
     const float4 *obs = reinterpret_cast<const float4 *>(s_cost + kObsOff);
 
     // own components of x0

@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(256) rollout_kernel(const StepParams p) {
     float *s_red = smem + L.red;
 
     const int tid = threadIdx.x, nt = blockDim.x;
+    wait_for_predecessor();
     for (int i = tid; i < p.T * NU; i += nt) s_u[i] = p.u_nom[i];
     Dyn::prepare(p.dyn_params, s_dyn, tid, nt);
     Cost::prepare(p.cost_params, s_cost, tid, nt);
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(256) rollout_kernel(const StepParams p) {
         p.S[k] = S;
     }
 
-    block_weight_tail(p, S, s_red);
+    block_weight_tail(p, S, k < p.K ? k : -1, s_red);
 }
 
 template <class Dyn, class Cost>
@@ -141,9 +142,11 @@ cudaError_t launch_rollout(const mppi_ctx &c, const StepParams &p) {
     dispatch(c.dyn_kind, c.cost_kind, c.nx, c.nu, [&](auto *d, auto *cst) {
         using D = std::remove_pointer_t<decltype(d)>;
         using C = std::remove_pointer_t<decltype(cst)>;
-        rollout_kernel<D, C><<<c.plan.rollout_blocks, c.plan.rollout_threads,
-                               c.plan.rollout_smem, c.stream>>>(p);
-        err = cudaGetLastError();
+        cudaLaunchAttribute attr[1];
+        const cudaLaunchConfig_t cfg = pdl_config(dim3(c.plan.rollout_blocks),
+                                                  dim3(c.plan.rollout_threads),
+                                                  c.plan.rollout_smem, c.stream, attr);
+        err = cudaLaunchKernelEx(&cfg, rollout_kernel<D, C>, p);
         return true;
     });
     return err;

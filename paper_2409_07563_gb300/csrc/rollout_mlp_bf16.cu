@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(256) bicycle_mlp_bf16_kernel(const StepParams 
     WarpTiles *tiles = reinterpret_cast<WarpTiles *>(s_red + kRedFloats);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5;
+    wait_for_predecessor();
     for (int i = tid; i < 2 * T; i += nt) s_u[i] = p.u_nom[i];
     CostmapSpeedCost::prepare(p.cost_params, s_cost, tid, nt);
     __syncthreads();
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(256) bicycle_mlp_bf16_kernel(const StepParams 
         S = J.value();
         p.S[k] = S;
     }
-    block_weight_tail(p, S, s_red);
+    block_weight_tail(p, S, active ? k : -1, s_red);
 }
 
 }  // namespace
@@ -241,9 +242,11 @@ cudaError_t mlp_bf16_prepare(const mppi_ctx &c) {
 }
 
 cudaError_t launch_mlp_bf16(const mppi_ctx &c, const StepParams &p) {
-    bicycle_mlp_bf16_kernel<<<c.plan.rollout_blocks, c.plan.rollout_threads, c.plan.rollout_smem,
-                              c.stream>>>(p);
-    return cudaGetLastError();
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = pdl_config(dim3(c.plan.rollout_blocks),
+                                              dim3(c.plan.rollout_threads), c.plan.rollout_smem,
+                                              c.stream, attr);
+    return cudaLaunchKernelEx(&cfg, bicycle_mlp_bf16_kernel, p);
 }
 
 }  // namespace mppi

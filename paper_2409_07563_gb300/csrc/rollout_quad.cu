@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(256) quad_group_kernel(const StepParams p) {
     float *s_cost = smem + round_up4(4 * T);
     float *s_red = s_cost + kQuadSmemCostFloats;
     const int tid = threadIdx.x, nt = blockDim.x;
+    wait_for_predecessor();
     for (int i = tid; i < 4 * T; i += nt) s_u[i] = p.u_nom[i];
     quad_prepare_cost(p.cost_params, kObstacles, s_cost, tid, nt);
     __syncthreads();
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(256) quad_group_kernel(const StepParams p) {
         S = tot;
         p.S[k] = S;
     }
-    block_weight_tail(p, S, s_red);
+    block_weight_tail(p, S, (k < p.K && r == 0) ? k : -1, s_red);
 }
 
 }  // namespace
@@ -87,13 +88,13 @@ cudaError_t quad_group_prepare(const mppi_ctx &c) {
 }
 
 cudaError_t launch_quad_group(const mppi_ctx &c, const StepParams &p) {
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = pdl_config(dim3(c.plan.rollout_blocks),
+                                              dim3(c.plan.rollout_threads), c.plan.rollout_smem,
+                                              c.stream, attr);
     if (c.cost_kind == MPPI_COST_QUAD_OBSTACLES)
-        quad_group_kernel<true><<<c.plan.rollout_blocks, c.plan.rollout_threads,
-                                  c.plan.rollout_smem, c.stream>>>(p);
-    else
-        quad_group_kernel<false><<<c.plan.rollout_blocks, c.plan.rollout_threads,
-                                   c.plan.rollout_smem, c.stream>>>(p);
-    return cudaGetLastError();
+        return cudaLaunchKernelEx(&cfg, quad_group_kernel<true>, p);
+    return cudaLaunchKernelEx(&cfg, quad_group_kernel<false>, p);
 }
 
 }  // namespace mppi

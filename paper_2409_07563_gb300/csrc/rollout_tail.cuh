@@ -10,68 +10,208 @@ namespace mppi {
 
 constexpr int kRedFloats = 64;
 
+// Kernel-to-kernel ordering with programmatic dependent launch: a kernel
+// launched with the programmatic-serialization attribute may start while its
+// predecessor finishes; it waits here before touching anything the
+// predecessor writes (a hardware dependency wait, not a spin).
+__device__ __forceinline__ void wait_for_predecessor() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void allow_successor_launch() {
+    asm volatile("griddepcontrol.launch_dependents;");
+}
+
+// Up to this many Philox blocks per thread, the last rollout block applies
+// the control update itself instead of leaving it to the update kernel.
+constexpr int kInlineUpdateCalls = 8;
+// A sample more than this many lambda above a cost that is at least the
+// global minimum has weight exactly zero in FP32 (exp underflows below
+// e^-103.3): only the other samples are kept as candidates.
+constexpr float kCandidateSpan = 110.f;
+// Candidates per last-block thread beyond which the last block leaves the
+// update to the update kernel, which then scans every sample.
+constexpr int kListPerThread = 8;
+// Order-preserving unsigned key of a float (for atomicMin on costs).
+__device__ __forceinline__ unsigned int float_key(float f) {
+    const unsigned int b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(unsigned int k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
 // Merge of the per-block partials by the last block: rho = min rho_b,
 // eta = sum eta_b exp(-(rho_b - rho)/lambda), same for eta2 with 2/lambda.
+// Then the list of samples with non-zero weight w_k = exp(-(S_k - rho)/lambda)
+// /eta, in sample order, built from the blocks' candidates, and -- when that
+// list is short -- the update u_new = u_nom + sum_k w_k eps_k itself.
 __device__ inline void finalize_weights(const StepParams &p, int nblocks, float *red) {
+    int *ired = reinterpret_cast<int *>(red);
     float rmin = __int_as_float(0x7f800000);
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-        rmin = fminf(rmin, __ldcg(p.partials + 3 * b));
+        rmin = fminf(rmin, __ldcg(p.partials + 4 * b));
     const float rho = block_min(rmin, red);
     FloatPair e1{0.f, 0.f}, e2{0.f, 0.f};
     if (is_finite(rho)) {
         for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-            const float rb = __ldcg(p.partials + 3 * b);
+            const float rb = __ldcg(p.partials + 4 * b);
             if (!is_finite(rb)) continue;
             const float f = expf(-(rb - rho) / p.lambda);
-            e1 = pair_add(e1, FloatPair{__ldcg(p.partials + 3 * b + 1) * f, 0.f});
-            e2 = pair_add(e2, FloatPair{__ldcg(p.partials + 3 * b + 2) * f * f, 0.f});
+            e1 = pair_add(e1, FloatPair{__ldcg(p.partials + 4 * b + 1) * f, 0.f});
+            e2 = pair_add(e2, FloatPair{__ldcg(p.partials + 4 * b + 2) * f * f, 0.f});
         }
     }
     const FloatPair eta = block_pair_sum(e1, red);
     const FloatPair eta2 = block_pair_sum(e2, red);
-    if (threadIdx.x == 0) {
-        float F, ess, eta_v = eta.hi + eta.lo;
-        const bool ok = is_finite(rho) && eta_v > 0.f;
-        if (ok) {
-            F = rho - p.lambda * logf(eta_v / static_cast<float>(p.K));
-            ess = eta_v * eta_v / (eta2.hi + eta2.lo);
-        } else {
-            F = __int_as_float(0x7f800000);
-            ess = 0.f;
-            eta_v = 0.f;
-            atomicOr(p.status, 1u << MPPI_ERR_NUMERIC);
+    const float eta_v = eta.hi + eta.lo;
+    const bool ok = is_finite(rho) && eta_v > 0.f;
+
+    // candidate counts of a contiguous range of blocks per thread, one scan
+    const int per = (nblocks + blockDim.x - 1) / blockDim.x;
+    const int b_begin = min(nblocks, static_cast<int>(threadIdx.x) * per);
+    const int b_end = min(nblocks, b_begin + per);
+    int mine = 0;
+    for (int b = b_begin; b < b_end; ++b) mine += static_cast<int>(__ldcg(p.partials + 4 * b + 3));
+    int n_cand;
+    const int base = block_exclusive_scan(mine, ired, n_cand);
+    const bool list_mode = !ok || n_cand <= kListPerThread * static_cast<int>(blockDim.x);
+    if (list_mode && ok) {
+        int pos = base;
+        for (int b = b_begin; b < b_end; ++b) {
+            const size_t off = static_cast<size_t>(b) * blockDim.x;
+            const int c = static_cast<int>(__ldcg(p.partials + 4 * b + 3));
+            for (int j = 0; j < c; ++j) {
+                const int k = __ldcg(p.cand + off + j);
+                p.nz[pos] = k;
+                p.w[pos] = expf(-(__ldcg(p.S + k) - rho) / p.lambda) / eta_v;
+                ++pos;
+            }
         }
-        p.scalars[0] = ok ? rho : __int_as_float(0x7f800000);
-        p.scalars[1] = eta_v;
+    }
+    // keep only the non-zero weights, in order (each thread owns a slice of
+    // at most kListPerThread entries of the candidate list)
+    int nnz = 0;
+    if (list_mode && ok) {
+        __syncthreads();
+        const int per_c = (n_cand + blockDim.x - 1) / blockDim.x;
+        const int c_begin = min(n_cand, static_cast<int>(threadIdx.x) * per_c);
+        const int c_end = min(n_cand, c_begin + per_c);
+        int kk[kListPerThread];
+        float ww[kListPerThread];
+        int keep = 0;
+#pragma unroll
+        for (int i = 0; i < kListPerThread; ++i) {
+            kk[i] = 0;
+            ww[i] = 0.f;
+            if (c_begin + i < c_end) {
+                kk[i] = p.nz[c_begin + i];
+                ww[i] = p.w[c_begin + i];
+                keep += ww[i] != 0.f;
+            }
+        }
+        int at = block_exclusive_scan(keep, ired, nnz);  // contains barriers
+#pragma unroll
+        for (int i = 0; i < kListPerThread; ++i) {
+            if (c_begin + i < c_end && ww[i] != 0.f) {
+                p.nz[at] = kk[i];
+                p.w[at] = ww[i];
+                ++at;
+            }
+        }
+    }
+    __syncthreads();
+    const int QT = (p.T + 3) / 4, Q = p.nu * QT;
+    const int per_thread = (Q + blockDim.x - 1) / blockDim.x;
+    const bool inline_update = list_mode && nnz * per_thread <= kInlineUpdateCalls;
+    if (inline_update) {
+        const NoiseKey nk = make_noise_key(p.seed, *p.counter);
+        for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+            const int j = q / QT, t0 = 4 * (q % QT);
+            const float sig = p.sigma[j];
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int idx = 0; idx < nnz; ++idx) {
+                const int k = p.nz[idx];
+                const float w = p.w[idx];
+                float z[4];
+                box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(q)), z);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] += w * (sig * z[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (t0 + i < p.T) {
+                    const int o = (t0 + i) * p.nu + j;
+                    p.u_new[o] = p.u_nom[o] + acc[i];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const float inf = __int_as_float(0x7f800000);
+        const float F = ok ? rho - p.lambda * logf(eta_v / static_cast<float>(p.K)) : inf;
+        const float ess = ok ? eta_v * eta_v / (eta2.hi + eta2.lo) : 0.f;
+        if (!ok) atomicOr(p.status, 1u << MPPI_ERR_NUMERIC);
+        p.scalars[0] = ok ? rho : inf;
+        p.scalars[1] = ok ? eta_v : 0.f;
         p.scalars[2] = F;
         p.scalars[3] = ess;
         p.scalars[4] = ok ? 1.f : 0.f;
+        p.scalars[5] = list_mode ? static_cast<float>(nnz) : -1.f;  // -1: scan every sample
+        p.scalars[6] = inline_update ? 1.f : 0.f;
+        *reinterpret_cast<unsigned int *>(p.scalars + 7) = 0xffffffffu;  // running minimum
         if (p.stats_out) {
             p.stats_out[0] = F;
             p.stats_out[1] = p.scalars[0];
-            p.stats_out[2] = eta_v;
+            p.stats_out[2] = p.scalars[1];
             p.stats_out[3] = ess;
+        }
+        if (inline_update) {  // the update kernel will find nothing to do
+            const unsigned long long step = *p.counter;
+            *p.last_step = step;
+            *p.counter = step + 1ull;
         }
         p.tickets[0] = 0u;  // ready for the next launch
     }
 }
 
 // Called by every thread of the block after its samples are done; S is this
-// thread's trajectory cost (+inf for threads that carry no sample).  The last
-// block to finish (atomic ticket; nobody waits) merges all partials into
-// rho, eta, F and ESS (Eq. 17-18, Eq. 4).
-__device__ inline void block_weight_tail(const StepParams &p, float S, float *s_red) {
+// thread's trajectory cost (+inf for threads that carry no sample) and k its
+// sample index (or -1).  The block folds its minimum into a running global
+// minimum m (atomicMin; m >= the final minimum) and keeps as candidates its
+// samples with S - m < 110 lambda -- every other sample has weight exactly
+// zero.  It leaves (rho_b, eta_b, eta2_b, n_cand) and its candidates; the last
+// block to finish (atomic ticket; nobody waits) merges them (Eq. 17-18, Eq. 4).
+__device__ inline void block_weight_tail(const StepParams &p, float S, int k, float *s_red) {
     const float Sf = is_finite(S) ? S : __int_as_float(0x7f800000);
+    if (k >= 0 && p.costs_out) p.costs_out[k] = S;
     const float rho_b = block_min(Sf, s_red);
     float e = 0.f;
     if (is_finite(Sf)) e = expf(-(Sf - rho_b) / p.lambda);
     const FloatPair eta_b = block_pair_sum(FloatPair{e, 0.f}, s_red);
     const FloatPair eta2_b = block_pair_sum(FloatPair{e * e, 0.f}, s_red);
+    __shared__ float s_gmin;
+    if (threadIdx.x == 0) {
+        float m = rho_b;
+        if (is_finite(rho_b)) {
+            const unsigned int old =
+                atomicMin(reinterpret_cast<unsigned int *>(p.scalars + 7), float_key(rho_b));
+            m = fminf(rho_b, key_float(old));
+        }
+        s_gmin = m;
+    }
+    __syncthreads();
+    const float gmin = s_gmin;
+    const bool cand = k >= 0 && is_finite(Sf) && (Sf - gmin) < kCandidateSpan * p.lambda;
+    int n_cand;
+    const int slot = block_exclusive_scan(cand ? 1 : 0, reinterpret_cast<int *>(s_red), n_cand);
+    if (cand) p.cand[static_cast<size_t>(blockIdx.x) * blockDim.x + slot] = k;
     __shared__ bool s_last;
     if (threadIdx.x == 0) {
-        p.partials[3 * blockIdx.x + 0] = rho_b;
-        p.partials[3 * blockIdx.x + 1] = eta_b.hi + eta_b.lo;
-        p.partials[3 * blockIdx.x + 2] = eta2_b.hi + eta2_b.lo;
+        p.partials[4 * blockIdx.x + 0] = rho_b;
+        p.partials[4 * blockIdx.x + 1] = eta_b.hi + eta_b.lo;
+        p.partials[4 * blockIdx.x + 2] = eta2_b.hi + eta2_b.lo;
+        p.partials[4 * blockIdx.x + 3] = static_cast<float>(n_cand);
         __threadfence();
         const unsigned int ticket = atomicAdd(p.tickets, 1u);
         s_last = (ticket == gridDim.x - 1);
@@ -81,6 +221,7 @@ __device__ inline void block_weight_tail(const StepParams &p, float S, float *s_
         __threadfence();
         finalize_weights(p, gridDim.x, s_red);
     }
+    allow_successor_launch();
 }
 
 }  // namespace mppi

@@ -1,33 +1,50 @@
 // update.cu -- weighted control update (step a5) and the noise diagnostic.
 //
-// u_new[t, j] = u_nom[t, j] + (sum_k exp(-(S_k - rho)/lambda) eps_{k,t,j}) / eta
-// for every (t, j) (Algorithm 1, control update).  eps is regenerated from the
-// same Philox counter the rollout used (bit-identical FP32 product
-// sigma_j * z), never read from memory: Philox block q holds channel
-// j = q / QT at steps 4 (q % QT) .. + 3.  Grid: (Philox-block tiles) x
-// (sample chunks); each thread walks samples of its chunk, each
-// block reduces its partial sums, and the last block to finish (atomic
-// ticket) adds the chunks in a fixed order, so the result is deterministic.
-// Samples whose weight underflows to exactly zero contribute exactly zero and
-// are skipped.
+// u_new[t, j] = u_nom[t, j] + sum_k w_k eps_{k,t,j} for every (t, j)
+// (Algorithm 1, control update), over the samples with non-zero weight that
+// the rollout's last block listed (a weight that underflowed to zero
+// contributes exactly zero).  eps is regenerated from the same Philox counter
+// the rollout used (bit-identical FP32 product sigma_j * z), never read from
+// memory: Philox block q holds channel j = q / QT at steps 4 (q % QT) .. + 3.
+// Grid: (Philox-block tiles) x (chunks of the non-zero list); each block
+// reduces its partial sums and the last block to finish (atomic ticket) adds
+// the chunks in a fixed order, so the result is deterministic.  When the
+// list was short the rollout already applied the update and every block
+// returns at once.
 #include "device_common.cuh"
 #include "mppi_internal.h"
+#include "rollout_tail.cuh"
 
 namespace mppi {
 namespace {
 
 template <int NU>
-__global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams p, int chunk_len) {
+__global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams p) {
     constexpr int QB = kUpdateQb;
     __shared__ float s_red[kUpdateThreads / kWarp][QB * 4];
     __shared__ bool s_last;
+    wait_for_predecessor();
+    const float rho = p.scalars[0], eta = p.scalars[1];
+    const bool valid = p.scalars[4] != 0.f;
+    const int kchunk = (p.K + gridDim.y - 1) / gridDim.y;
+    if (p.weights_out && blockIdx.x == 0) {
+        const int k_end = min(p.K, (blockIdx.y + 1) * kchunk);
+        for (int k = blockIdx.y * kchunk + threadIdx.x; k < k_end; k += blockDim.x) {
+            const float S = p.S[k];
+            p.weights_out[k] = valid && is_finite(S) ? expf(-(S - rho) / p.lambda) / eta : 0.f;
+        }
+    }
+    if (p.scalars[6] != 0.f) return;  // the rollout's last block applied the update
     const int QT = (p.T + 3) / 4;
     const int Q = NU * QT;
     const int q0 = blockIdx.x * QB;
-    const int k_begin = blockIdx.y * chunk_len;
-    const int k_end = min(p.K, k_begin + chunk_len);
-    const float rho = p.scalars[0], eta = p.scalars[1];
-    const bool valid = p.scalars[4] != 0.f;
+    // list mode: the non-zero-weight samples listed by the rollout; otherwise
+    // (-1) every sample of this chunk, weight recomputed from its cost
+    const int nnz = static_cast<int>(p.scalars[5]);
+    const bool list = nnz >= 0;
+    const int n = list ? nnz : p.K;
+    const int len = (n + gridDim.y - 1) / gridDim.y;
+    const int i_begin = blockIdx.y * len, i_end = min(n, i_begin + len);
     const NoiseKey nk = make_noise_key(p.seed, *p.counter);
 
     float acc[QB][4];
@@ -36,15 +53,18 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[a][i] = 0.f;
 
-    for (int k = k_begin + threadIdx.x; k < k_end; k += blockDim.x) {
-        const float S = p.S[k];
-        float e = 0.f;
-        if (valid && is_finite(S)) e = expf(-(S - rho) / p.lambda);
-        if (blockIdx.x == 0) {
-            if (p.weights_out) p.weights_out[k] = valid ? e / eta : 0.f;
-            if (p.costs_out) p.costs_out[k] = S;
+    for (int idx = i_begin + threadIdx.x; idx < i_end; idx += blockDim.x) {
+        int k;
+        float w;
+        if (list) {
+            k = __ldcg(p.nz + idx);
+            w = __ldcg(p.w + idx);
+        } else {
+            k = idx;
+            const float S = p.S[k];
+            w = valid && is_finite(S) ? expf(-(S - rho) / p.lambda) / eta : 0.f;
+            if (w == 0.f) continue;
         }
-        if (e == 0.f) continue;
 #pragma unroll
         for (int a = 0; a < QB; ++a) {
             const int q = q0 + a;
@@ -53,7 +73,7 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
                 box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(q)), z);
                 const float sig = p.sigma[q / QT];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) acc[a][i] += e * (sig * z[i]);
+                for (int i = 0; i < 4; ++i) acc[a][i] += w * (sig * z[i]);
             }
         }
     }
@@ -85,7 +105,6 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
     __threadfence();
 
     // last block: combine chunks in order and write u_new
-    const float inv_eta = valid ? 1.f / eta : 0.f;
     for (int el = threadIdx.x; el < 4 * Q; el += blockDim.x) {
         const int q = el / 4, j = q / QT, t = 4 * (q % QT) + el % 4;
         if (t >= p.T) continue;
@@ -93,7 +112,7 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
         for (int c = 0; c < static_cast<int>(gridDim.y); ++c)
             sum += __ldcg(p.upartials + (static_cast<size_t>(c) * Q) * 4 + el);
         const int o = t * NU + j;
-        p.u_new[o] = p.u_nom[o] + (valid ? sum * inv_eta : 0.f);
+        p.u_new[o] = p.u_nom[o] + sum;
     }
     if (threadIdx.x == 0) {
         const unsigned long long step = *p.counter;
@@ -125,17 +144,32 @@ __global__ void sample_noise_kernel(uint64_t seed, uint64_t step, int K, int Q, 
 
 }  // namespace
 
+cudaLaunchConfig_t pdl_config(dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              cudaLaunchAttribute *attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
 cudaError_t launch_update(const mppi_ctx &c, const StepParams &p) {
-    const dim3 grid(c.plan.update_qtiles, c.plan.update_chunks);
-    const int len = c.plan.update_chunk_len;
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg =
+        pdl_config(dim3(c.plan.update_qtiles, c.plan.update_chunks), dim3(kUpdateThreads), 0,
+                   c.stream, attr);
     switch (c.nu) {
-    case 1: update_kernel<1><<<grid, kUpdateThreads, 0, c.stream>>>(p, len); break;
-    case 2: update_kernel<2><<<grid, kUpdateThreads, 0, c.stream>>>(p, len); break;
-    case 3: update_kernel<3><<<grid, kUpdateThreads, 0, c.stream>>>(p, len); break;
-    case 4: update_kernel<4><<<grid, kUpdateThreads, 0, c.stream>>>(p, len); break;
+    case 1: return cudaLaunchKernelEx(&cfg, update_kernel<1>, p);
+    case 2: return cudaLaunchKernelEx(&cfg, update_kernel<2>, p);
+    case 3: return cudaLaunchKernelEx(&cfg, update_kernel<3>, p);
+    case 4: return cudaLaunchKernelEx(&cfg, update_kernel<4>, p);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_sample_noise(uint64_t seed, uint64_t step, int K, int Q, uint32_t *bits,
