@@ -143,9 +143,15 @@ typedef struct {
     int beta;                 /* importance-sampling term: 1 (default) or 0 */
     int precision;            /* mppi_precision (default FP32) */
     uint64_t seed;            /* Philox key (default 0) */
-    int block_threads;        /* rollout block size (multiple of 32, <= 256); 0 = automatic */
+    int block_threads;        /* rollout block size (multiple of 32, <= 256; variant 3:
+                                 multiple of 64, <= 512; variant 4: 128 or 256);
+                                 0 = automatic */
     int rollout_variant;      /* 0 automatic, 1 one sample per thread, 2 four lanes per
-                                 sample (QUADROTOR with at most 32 obstacles) */
+                                 sample, 3 four lanes per sample with a dynamics warp
+                                 and a cost warp per eight samples, 4 one sample per
+                                 thread with a dynamics warp, two noise warps and a
+                                 cost warp per 32 samples (2-4: QUADROTOR with at most
+                                 32 obstacles) */
     int reserved[6];
 } mppi_options;
 

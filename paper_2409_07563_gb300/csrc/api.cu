@@ -97,16 +97,42 @@ void free_ctx(mppi_ctx *c) {
 
 void plan_launch(mppi_ctx &c) {
     mppi::LaunchPlan &pl = c.plan;
-    const bool group = mppi::quad_group_applicable(c) && c.variant_opt != mppi::kVariantGeneric;
+    const bool quad = mppi::quad_group_applicable(c) && c.variant_opt != mppi::kVariantGeneric;
+    // Automatic: one sample per thread with four warp roles per 32 samples
+    // (measured on GB300: 62.7 us per step at K = 8192, T = 150 against 70.6
+    // for the four-lane warp pairs and 109 for the four-lane single warps;
+    // 3.1e10 against 2.4e10 rollout-steps/s at K = 524288).
+    const int asked = c.variant_opt == 0 ? mppi::kVariantQuadPair : c.variant_opt;
+    const int roles = mppi::quad_pair_roles(c);  // warps per 32 samples
+    const bool pair1 = quad && asked == mppi::kVariantQuadPair &&
+                       c.block_threads % (32 * roles) == 0 && mppi::quad_pair_applicable(c);
+    const bool split = quad && !pair1 && asked != mppi::kVariantQuadGroup &&
+                       c.block_threads % 64 == 0;
+    const bool group = quad && !pair1 && !split;
     const bool mlp_tc = c.precision == MPPI_PREC_BF16_MLP;
-    pl.variant = mlp_tc ? mppi::kVariantMlpBf16
-                        : group ? mppi::kVariantQuadGroup : mppi::kVariantGeneric;
-    const int lanes = group ? 4 : 1;             // threads per sample
+    pl.variant = mlp_tc  ? mppi::kVariantMlpBf16
+                 : pair1 ? mppi::kVariantQuadPair
+                 : split ? mppi::kVariantQuadSplit
+                 : group ? mppi::kVariantQuadGroup
+                         : mppi::kVariantGeneric;
+    const int lanes = split ? 8 : pair1 ? roles : group ? 4 : 1;  // threads per sample
     const long threads_needed = static_cast<long>(c.K) * lanes;
     if (c.block_threads > 0) {
         pl.rollout_threads = c.block_threads;
     } else if (mlp_tc) {
         pl.rollout_threads = 64;                 // two warps of 32 samples
+    } else if (pair1) {
+        // warp groups of 32 samples spread over every SM first, at most two
+        // groups per block (K = 8192: 256 groups, two per block on 128 SMs)
+        const long groups = (static_cast<long>(c.K) + 31) / 32;
+        const long per_sm = (groups + c.num_sms - 1) / c.num_sms;
+        pl.rollout_threads = 32 * roles * static_cast<int>(std::min(2L, std::max(1L, per_sm)));
+    } else if (split) {
+        // one block per SM while the pairs fit eight to an SM, spread evenly
+        // (K = 8192: 1024 pairs, seven per block on 147 SMs); else four pairs
+        const long pairs = (static_cast<long>(c.K) + 7) / 8;
+        const long per_sm = (pairs + c.num_sms - 1) / c.num_sms;
+        pl.rollout_threads = per_sm <= 8 ? static_cast<int>(64 * per_sm) : 256;
     } else if (group) {
         pl.rollout_threads = 64;
     } else {
@@ -243,10 +269,13 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     for (int j = 0; j < nu; ++j)
         if (!std::isfinite(sigma[j]) || sigma[j] < 0.f) return MPPI_ERR_INVALID_ARG;
     if (o.beta != 0 && o.beta != 1) return MPPI_ERR_INVALID_ARG;
-    if (o.block_threads < 0 || o.block_threads > 256 || o.block_threads % 32 != 0)
+    if (o.block_threads < 0 || o.block_threads % 32 != 0 ||
+        o.block_threads > (o.rollout_variant == 3 ? 512 : 256))
         return MPPI_ERR_INVALID_ARG;
-    if (o.rollout_variant < 0 || o.rollout_variant > 2) return MPPI_ERR_INVALID_ARG;
-    if (o.rollout_variant == 2 &&
+    if (o.rollout_variant < 0 || o.rollout_variant > 4) return MPPI_ERR_INVALID_ARG;
+    if (o.rollout_variant == 3 && o.block_threads % 64 != 0) return MPPI_ERR_INVALID_ARG;
+    if (o.rollout_variant == 4 && o.block_threads % 128 != 0) return MPPI_ERR_INVALID_ARG;
+    if (o.rollout_variant >= 2 &&
         (dyn->kind != MPPI_DYN_QUADROTOR ||
          (cost->kind == MPPI_COST_QUAD_OBSTACLES && cost->n_params > 33 + 4 * 32)))
         return MPPI_ERR_UNSUPPORTED;
@@ -299,7 +328,7 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     if ((e = dalloc(&c->scr.S, K)) != cudaSuccess ||
         (e = dalloc(&c->scr.w, K)) != cudaSuccess ||
         (e = dalloc(&c->scr.nz, K)) != cudaSuccess ||
-        (e = dalloc(&c->scr.cand, 4 * static_cast<size_t>(K) + 256)) != cudaSuccess ||
+        (e = dalloc(&c->scr.cand, 2 * (static_cast<size_t>(K) + 256))) != cudaSuccess ||
         (e = dalloc(&c->scr.partials, 4 * max_blocks)) != cudaSuccess ||
         (e = dalloc(&c->scr.upartials, static_cast<size_t>(mppi::kMaxUpdateChunks) * Q * 4)) != cudaSuccess ||
         (e = dalloc(&c->scr.scalars, 8)) != cudaSuccess ||
@@ -341,6 +370,8 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     }
     c->plan.rollout_smem =
         c->plan.variant == mppi::kVariantQuadGroup ? mppi::quad_group_smem_bytes(*c)
+        : c->plan.variant == mppi::kVariantQuadSplit ? mppi::quad_split_smem_bytes(*c, c->plan.rollout_threads)
+        : c->plan.variant == mppi::kVariantQuadPair ? mppi::quad_pair_smem_bytes(*c, c->plan.rollout_threads)
         : c->plan.variant == mppi::kVariantMlpBf16 ? mppi::mlp_bf16_smem_bytes(*c, c->plan.rollout_threads)
                                                    : mppi::rollout_smem_bytes(*c);
     int max_smem = 0;
@@ -351,6 +382,8 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     }
     if ((e = mppi::rollout_prepare(*c)) != cudaSuccess ||
         (c->plan.variant == mppi::kVariantQuadGroup && (e = mppi::quad_group_prepare(*c)) != cudaSuccess) ||
+        (c->plan.variant == mppi::kVariantQuadSplit && (e = mppi::quad_split_prepare(*c)) != cudaSuccess) ||
+        (c->plan.variant == mppi::kVariantQuadPair && (e = mppi::quad_pair_prepare(*c)) != cudaSuccess) ||
         (c->plan.variant == mppi::kVariantMlpBf16 && (e = mppi::mlp_bf16_prepare(*c)) != cudaSuccess)) {
         free_ctx(c);
         return MPPI_ERR_CUDA;
@@ -387,6 +420,8 @@ mppi_status mppi_step(mppi_ctx *ctx, const float *x0_d, const float *u_nom_d, fl
     {
         ProfScope ps(ctx, MPPI_PROF_ROLLOUT);
         e = ctx->plan.variant == mppi::kVariantQuadGroup ? mppi::launch_quad_group(*ctx, p)
+            : ctx->plan.variant == mppi::kVariantQuadSplit ? mppi::launch_quad_split(*ctx, p)
+            : ctx->plan.variant == mppi::kVariantQuadPair ? mppi::launch_quad_pair(*ctx, p)
             : ctx->plan.variant == mppi::kVariantMlpBf16 ? mppi::launch_mlp_bf16(*ctx, p)
                                                          : mppi::launch_rollout(*ctx, p);
     }

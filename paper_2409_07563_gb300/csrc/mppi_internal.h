@@ -26,7 +26,7 @@ struct Scratch {
     float *S = nullptr;                 // [K] trajectory costs
     float *w = nullptr;                 // [K] weights of the listed samples (parallel to nz)
     int *nz = nullptr;                  // [K] samples with non-zero weight, in index order
-    int *cand = nullptr;                // [4K] per-block weight candidates
+    int *cand = nullptr;                // [2 (K + 256)] per-block weight candidates (k, S_k bits)
     float *partials = nullptr;          // [4 * max rollout blocks] (rho_b, eta_b, eta2_b, n_cand)
     float *upartials = nullptr;         // [kMaxUpdateChunks * Q * 4] update partial sums
     float *scalars = nullptr;           // [8] rho, eta, F, ess, valid, nnz, update-done
@@ -63,7 +63,13 @@ struct StepParams {
     unsigned long long *counter, *last_step;
 };
 
-enum RolloutVariant { kVariantGeneric = 1, kVariantQuadGroup = 2, kVariantMlpBf16 = 3 };
+enum RolloutVariant {
+    kVariantGeneric = 1,
+    kVariantQuadGroup = 2,
+    kVariantQuadSplit = 3,
+    kVariantQuadPair = 4,
+    kVariantMlpBf16 = 5
+};
 
 struct LaunchPlan {
     int variant = kVariantGeneric;
@@ -128,6 +134,16 @@ bool quad_group_applicable(const mppi_ctx &c);
 size_t quad_group_smem_bytes(const mppi_ctx &c);
 cudaError_t quad_group_prepare(const mppi_ctx &c);
 cudaError_t launch_quad_group(const mppi_ctx &c, const StepParams &p);
+// rollout_quad_split.cu: a dynamics warp and a cost warp per eight samples
+size_t quad_split_smem_bytes(const mppi_ctx &c, int threads);
+cudaError_t quad_split_prepare(const mppi_ctx &c);
+cudaError_t launch_quad_split(const mppi_ctx &c, const StepParams &p);
+// rollout_quad_pair.cu: one sample per thread, dynamics / cost / crash warps per 32 samples
+bool quad_pair_applicable(const mppi_ctx &c);
+int quad_pair_roles(const mppi_ctx &c);  // warps per 32 samples: 3 with obstacles, else 2
+size_t quad_pair_smem_bytes(const mppi_ctx &c, int threads);
+cudaError_t quad_pair_prepare(const mppi_ctx &c);
+cudaError_t launch_quad_pair(const mppi_ctx &c, const StepParams &p);
 // rollout_mlp_bf16.cu: bicycle + MLP on the tensor cores
 size_t mlp_bf16_smem_bytes(const mppi_ctx &c, int threads);
 cudaError_t mlp_bf16_prepare(const mppi_ctx &c);

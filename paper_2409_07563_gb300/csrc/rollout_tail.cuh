@@ -43,22 +43,50 @@ __device__ __forceinline__ float key_float(unsigned int k) {
 // Merge of the per-block partials by the last block: rho = min rho_b,
 // eta = sum eta_b exp(-(rho_b - rho)/lambda), same for eta2 with 2/lambda.
 // Then the list of samples with non-zero weight w_k = exp(-(S_k - rho)/lambda)
-// /eta, in sample order, built from the blocks' candidates, and -- when that
-// list is short -- the update u_new = u_nom + sum_k w_k eps_k itself.
-__device__ inline void finalize_weights(const StepParams &p, int nblocks, float *red) {
+// /eta, in sample order, built from the blocks' candidates (k, S_k), and --
+// when that list is short -- the update u_new = u_nom + sum_k w_k eps_k itself.
+//
+// While the grid has no more blocks than this block has threads, every
+// global read of the merge is one parallel round trip: each thread loads one
+// block's partials, then at most kListPerThread candidate pairs, located by a
+// search in the blocks' candidate offsets; the non-zero weights are compacted
+// in registers.  Larger grids walk contiguous block ranges per thread.
+constexpr int kMaxFinalizeThreads = 512;
+__device__ inline void finalize_weights(const StepParams &p, int nblocks, int cand_stride,
+                                        float *red) {
+    __shared__ int s_off[kMaxFinalizeThreads + 1];  // candidate offset of each block
+    __shared__ int s_nzk[kInlineUpdateCalls];       // a short non-zero list for the inline update
+    __shared__ float s_nzw[kInlineUpdateCalls];
     int *ired = reinterpret_cast<int *>(red);
-    float rmin = __int_as_float(0x7f800000);
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-        rmin = fminf(rmin, __ldcg(p.partials + 4 * b));
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const float inf = __int_as_float(0x7f800000);
+    const unsigned long long step = __ldcg(p.counter);
+    const bool fast = nblocks <= nt;
+    const float4 *part4 = reinterpret_cast<const float4 *>(p.partials);
+    const int2 *cand2 = reinterpret_cast<const int2 *>(p.cand);
+
+    float4 mine = make_float4(inf, 0.f, 0.f, 0.f);  // (rho_b, eta_b, eta2_b, n_cand_b)
+    if (fast && tid < nblocks) mine = __ldcg(part4 + tid);
+    float rmin = mine.x;
+    if (!fast)
+        for (int b = tid; b < nblocks; b += nt) rmin = fminf(rmin, __ldcg(p.partials + 4 * b));
     const float rho = block_min(rmin, red);
     FloatPair e1{0.f, 0.f}, e2{0.f, 0.f};
     if (is_finite(rho)) {
-        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-            const float rb = __ldcg(p.partials + 4 * b);
-            if (!is_finite(rb)) continue;
-            const float f = expf(-(rb - rho) / p.lambda);
-            e1 = pair_add(e1, FloatPair{__ldcg(p.partials + 4 * b + 1) * f, 0.f});
-            e2 = pair_add(e2, FloatPair{__ldcg(p.partials + 4 * b + 2) * f * f, 0.f});
+        if (fast) {
+            if (is_finite(mine.x)) {
+                const float f = expf(-(mine.x - rho) / p.lambda);
+                e1 = FloatPair{mine.y * f, 0.f};
+                e2 = FloatPair{mine.z * f * f, 0.f};
+            }
+        } else {
+            for (int b = tid; b < nblocks; b += nt) {
+                const float4 q = __ldcg(part4 + b);
+                if (!is_finite(q.x)) continue;
+                const float f = expf(-(q.x - rho) / p.lambda);
+                e1 = pair_add(e1, FloatPair{q.y * f, 0.f});
+                e2 = pair_add(e2, FloatPair{q.z * f * f, 0.f});
+            }
         }
     }
     const FloatPair eta = block_pair_sum(e1, red);
@@ -66,35 +94,84 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, float 
     const float eta_v = eta.hi + eta.lo;
     const bool ok = is_finite(rho) && eta_v > 0.f;
 
-    // candidate counts of a contiguous range of blocks per thread, one scan
-    const int per = (nblocks + blockDim.x - 1) / blockDim.x;
-    const int b_begin = min(nblocks, static_cast<int>(threadIdx.x) * per);
+    // candidate counts: one block per thread (fast) or a contiguous range
+    const int per = fast ? 1 : (nblocks + nt - 1) / nt;
+    const int b_begin = min(nblocks, tid * per);
     const int b_end = min(nblocks, b_begin + per);
-    int mine = 0;
-    for (int b = b_begin; b < b_end; ++b) mine += static_cast<int>(__ldcg(p.partials + 4 * b + 3));
+    int mine_cnt = 0;
+    if (fast)
+        mine_cnt = tid < nblocks ? static_cast<int>(mine.w) : 0;
+    else
+        for (int b = b_begin; b < b_end; ++b) mine_cnt += static_cast<int>(__ldcg(p.partials + 4 * b + 3));
     int n_cand;
-    const int base = block_exclusive_scan(mine, ired, n_cand);
-    const bool list_mode = !ok || n_cand <= kListPerThread * static_cast<int>(blockDim.x);
-    if (list_mode && ok) {
+    const int base = block_exclusive_scan(mine_cnt, ired, n_cand);
+    const bool list_mode = !ok || n_cand <= kListPerThread * nt;
+    int nnz = 0;
+    if (list_mode && ok && fast) {
+        if (tid < nblocks) s_off[tid] = base;
+        if (tid == 0) s_off[nblocks] = n_cand;
+        __syncthreads();
+        // positions [i0, i1) of the candidate list, in sample order
+        const int pc = (n_cand + nt - 1) / nt;
+        const int i0 = min(n_cand, tid * pc), i1 = min(n_cand, i0 + pc);
+        int b = 0;
+        if (i0 < i1) {  // last block whose offset is <= i0 (empty blocks share offsets)
+            int lo = 0, hi = nblocks - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= i0) lo = mid; else hi = mid - 1;
+            }
+            b = lo;
+        }
+        int2 e[kListPerThread];
+#pragma unroll
+        for (int j = 0; j < kListPerThread; ++j) {
+            const int i = i0 + j;
+            e[j] = make_int2(0, 0);
+            if (i < i1) {
+                while (i >= s_off[b + 1]) ++b;
+                e[j] = __ldcg(cand2 + static_cast<size_t>(b) * cand_stride + (i - s_off[b]));
+            }
+        }
+        float w[kListPerThread];
+        int keep = 0;
+#pragma unroll
+        for (int j = 0; j < kListPerThread; ++j) {
+            w[j] = 0.f;
+            if (i0 + j < i1) {
+                w[j] = expf(-(__int_as_float(e[j].y) - rho) / p.lambda) / eta_v;
+                keep += w[j] != 0.f;
+            }
+        }
+        int at = block_exclusive_scan(keep, ired, nnz);  // contains barriers
+#pragma unroll
+        for (int j = 0; j < kListPerThread; ++j) {
+            if (i0 + j < i1 && w[j] != 0.f) {
+                p.nz[at] = e[j].x;
+                p.w[at] = w[j];
+                if (at < kInlineUpdateCalls) {
+                    s_nzk[at] = e[j].x;
+                    s_nzw[at] = w[j];
+                }
+                ++at;
+            }
+        }
+    } else if (list_mode && ok) {
+        // large grid: list every candidate, then keep the non-zero ones
         int pos = base;
         for (int b = b_begin; b < b_end; ++b) {
-            const size_t off = static_cast<size_t>(b) * blockDim.x;
+            const size_t off = static_cast<size_t>(b) * cand_stride;
             const int c = static_cast<int>(__ldcg(p.partials + 4 * b + 3));
             for (int j = 0; j < c; ++j) {
-                const int k = __ldcg(p.cand + off + j);
-                p.nz[pos] = k;
-                p.w[pos] = expf(-(__ldcg(p.S + k) - rho) / p.lambda) / eta_v;
+                const int2 ent = __ldcg(cand2 + off + j);
+                p.nz[pos] = ent.x;
+                p.w[pos] = expf(-(__int_as_float(ent.y) - rho) / p.lambda) / eta_v;
                 ++pos;
             }
         }
-    }
-    // keep only the non-zero weights, in order (each thread owns a slice of
-    // at most kListPerThread entries of the candidate list)
-    int nnz = 0;
-    if (list_mode && ok) {
         __syncthreads();
-        const int per_c = (n_cand + blockDim.x - 1) / blockDim.x;
-        const int c_begin = min(n_cand, static_cast<int>(threadIdx.x) * per_c);
+        const int per_c = (n_cand + nt - 1) / nt;
+        const int c_begin = min(n_cand, tid * per_c);
         const int c_end = min(n_cand, c_begin + per_c);
         int kk[kListPerThread];
         float ww[kListPerThread];
@@ -115,23 +192,28 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, float 
             if (c_begin + i < c_end && ww[i] != 0.f) {
                 p.nz[at] = kk[i];
                 p.w[at] = ww[i];
+                if (at < kInlineUpdateCalls) {
+                    s_nzk[at] = kk[i];
+                    s_nzw[at] = ww[i];
+                }
                 ++at;
             }
         }
     }
     __syncthreads();
     const int QT = (p.T + 3) / 4, Q = p.nu * QT;
-    const int per_thread = (Q + blockDim.x - 1) / blockDim.x;
+    const int per_thread = (Q + nt - 1) / nt;
+    // (per_thread >= 1, so an inline list has at most kInlineUpdateCalls entries)
     const bool inline_update = list_mode && nnz * per_thread <= kInlineUpdateCalls;
     if (inline_update) {
-        const NoiseKey nk = make_noise_key(p.seed, *p.counter);
-        for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+        const NoiseKey nk = make_noise_key(p.seed, step);
+        for (int q = tid; q < Q; q += nt) {
             const int j = q / QT, t0 = 4 * (q % QT);
             const float sig = p.sigma[j];
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
             for (int idx = 0; idx < nnz; ++idx) {
-                const int k = p.nz[idx];
-                const float w = p.w[idx];
+                const int k = s_nzk[idx];
+                const float w = s_nzw[idx];
                 float z[4];
                 box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(q)), z);
 #pragma unroll
@@ -147,8 +229,7 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, float 
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const float inf = __int_as_float(0x7f800000);
+    if (tid == 0) {
         const float F = ok ? rho - p.lambda * logf(eta_v / static_cast<float>(p.K)) : inf;
         const float ess = ok ? eta_v * eta_v / (eta2.hi + eta2.lo) : 0.f;
         if (!ok) atomicOr(p.status, 1u << MPPI_ERR_NUMERIC);
@@ -167,7 +248,6 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, float 
             p.stats_out[3] = ess;
         }
         if (inline_update) {  // the update kernel will find nothing to do
-            const unsigned long long step = *p.counter;
             *p.last_step = step;
             *p.counter = step + 1ull;
         }
@@ -177,12 +257,14 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, float 
 
 // Called by every thread of the block after its samples are done; S is this
 // thread's trajectory cost (+inf for threads that carry no sample) and k its
-// sample index (or -1).  The block folds its minimum into a running global
+// sample index (or -1); cand_stride bounds the samples a block carries (its
+// candidate slots start at blockIdx.x * cand_stride).  The block folds its minimum into a running global
 // minimum m (atomicMin; m >= the final minimum) and keeps as candidates its
 // samples with S - m < 110 lambda -- every other sample has weight exactly
 // zero.  It leaves (rho_b, eta_b, eta2_b, n_cand) and its candidates; the last
 // block to finish (atomic ticket; nobody waits) merges them (Eq. 17-18, Eq. 4).
-__device__ inline void block_weight_tail(const StepParams &p, float S, int k, float *s_red) {
+__device__ inline void block_weight_tail(const StepParams &p, float S, int k, float *s_red,
+                                         int cand_stride) {
     const float Sf = is_finite(S) ? S : __int_as_float(0x7f800000);
     if (k >= 0 && p.costs_out) p.costs_out[k] = S;
     const float rho_b = block_min(Sf, s_red);
@@ -205,7 +287,9 @@ __device__ inline void block_weight_tail(const StepParams &p, float S, int k, fl
     const bool cand = k >= 0 && is_finite(Sf) && (Sf - gmin) < kCandidateSpan * p.lambda;
     int n_cand;
     const int slot = block_exclusive_scan(cand ? 1 : 0, reinterpret_cast<int *>(s_red), n_cand);
-    if (cand) p.cand[static_cast<size_t>(blockIdx.x) * blockDim.x + slot] = k;
+    if (cand)
+        reinterpret_cast<int2 *>(p.cand)[static_cast<size_t>(blockIdx.x) * cand_stride + slot] =
+            make_int2(k, __float_as_int(Sf));
     __shared__ bool s_last;
     if (threadIdx.x == 0) {
         p.partials[4 * blockIdx.x + 0] = rho_b;
@@ -219,7 +303,7 @@ __device__ inline void block_weight_tail(const StepParams &p, float S, int k, fl
     __syncthreads();
     if (s_last) {
         __threadfence();
-        finalize_weights(p, gridDim.x, s_red);
+        finalize_weights(p, gridDim.x, cand_stride, s_red);
     }
     allow_successor_launch();
 }

@@ -137,14 +137,14 @@ def test_cartpole_spread_weights(m, lam):
         assert d["ess"] > 10
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_quadrotor_config_full(m, variant):
     p = as_f32_problem(W.quadrotor())
     g, _ = run_gpu(m, p, rollout_variant=variant)
     compare(p, g)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 @pytest.mark.parametrize("lam", [200.0, 2000.0])
 def test_quadrotor_spread_weights_no_is(m, lam, variant):
     p = as_f32_problem(W.quadrotor(lam=lam, beta=0))
@@ -160,13 +160,46 @@ def test_quadrotor_lane_groups_block_sizes(m, threads):
     compare(p, g)
 
 
+@pytest.mark.parametrize("threads", [64, 128, 256, 448, 512])
+def test_quadrotor_warp_pairs_block_sizes(m, threads):
+    # a dynamics warp and a cost warp per eight samples; K ragged against the
+    # block's samples, T not a multiple of the 8-step ring half
+    p = as_f32_problem(W.quadrotor(K=1001, T=37, lam=300.0, beta=0))
+    g, _ = run_gpu(m, p, rollout_variant=3, block_threads=threads)
+    compare(p, g)
+
+
+@pytest.mark.parametrize("threads", [128, 256])
+def test_quadrotor_one_lane_warp_groups_block_sizes(m, threads):
+    # one sample per thread, dynamics / two noise / cost warps per 32 samples; K
+    # ragged against the block's samples, T not a multiple of the 4-step half
+    p = as_f32_problem(W.quadrotor(K=1001, T=37, lam=300.0, beta=0))
+    g, _ = run_gpu(m, p, rollout_variant=4, block_threads=threads)
+    compare(p, g)
+
+
+def test_quadrotor_one_lane_warp_groups_large_k(m):
+    # more groups than two per SM: the build that keeps the spheres in shared
+    # memory (two blocks per SM); checked at rows the oracle computes alone
+    p = as_f32_problem(W.quadrotor(K=40000, T=20, lam=300.0, beta=0))
+    g, _ = run_gpu(m, p, rollout_variant=4)
+    compare(p, g)
+
+
+@pytest.mark.parametrize("variant,threads", [(3, 96), (4, 64), (4, 192), (4, 384)])
+def test_quadrotor_warp_groups_need_whole_groups(m, variant, threads):
+    p = W.quadrotor(K=100, T=10)
+    with pytest.raises(m.MPPIError):
+        m.MPPI.from_problem(p, rollout_variant=variant, block_threads=threads)
+
+
 def test_quadrotor_lane_groups_quadratic_cost_only(m):
     base = W.quadrotor(K=700, T=50, lam=100.0, beta=1)
     q = dict(base)
     q["cost_kind"] = W.COST_QUADRATIC
     q["cost_params"] = base["cost_params"][:31].copy()
     p = as_f32_problem(q)
-    for variant in (1, 2):
+    for variant in (1, 2, 3, 4):
         g, _ = run_gpu(m, p, rollout_variant=variant)
         compare(p, g)
 
@@ -187,8 +220,8 @@ def test_cartpole_ragged(m, K, T):
     compare(p, g)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
-@pytest.mark.parametrize("K,T", [(777, 23), (129, 150), (3, 5)])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("K,T", [(777, 23), (129, 150), (3, 5), (9, 8), (17, 1)])
 def test_quadrotor_ragged(m, K, T, variant):
     p = as_f32_problem(W.quadrotor(K=K, T=T, lam=300.0, beta=0))
     g, _ = run_gpu(m, p, rollout_variant=variant)
