@@ -55,7 +55,8 @@ FLOPS_PER_ROLLOUT_STEP = {
     "bicycle": 9604 + 20 + 15 + 14 + 4,
 }
 KERNEL_NAME = {
-    "quadrotor": "quad_split_kernel<true> (a dynamics warp and a cost warp per eight samples)",
+    "quadrotor": "quad_pair_kernel<true,false> (one sample per thread; dynamics, two noise and "
+                 "a cost warp per 32 samples)",
     "cartpole": "rollout_kernel<CartpoleDyn, QuadraticCost<4,1>>",
     "bicycle": "rollout_kernel<BicycleMlpDyn, CostmapSpeedCost>",
 }

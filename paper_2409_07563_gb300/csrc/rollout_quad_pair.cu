@@ -49,7 +49,8 @@ struct QuadPairConst {
 
 namespace {
 
-constexpr int kPairH = 4;  // steps per ring half: one Philox block per channel
+constexpr int kPairH = 4;  // steps per ring half (whole Philox blocks of four steps)
+static_assert(kPairH % 4 == 0, "a ring half holds whole noise blocks");
 constexpr int kRingXPair = 2 * kPairH * 4 * kWarp;  // float4: [half][step][group][lane]
 constexpr int kRingVPair = 2 * kPairH * kWarp;      // float4: [half][step][lane]
 
@@ -183,9 +184,16 @@ __device__ __forceinline__ FloatPair pair_noise(const StepParams &p, const QuadP
     auto controls = [&](int hc) {
         float2 *vb = reinterpret_cast<float2 *>(ring_v + (hc & 1) * kPairH * kWarp) + (j0 >> 1);
         const int nc = min(kPairH, T - hc * kPairH);
-        float z0[4], z1[4];
-        box_muller(noise_bits(nk, k, static_cast<uint32_t>(j0 * QT + hc)), z0);
-        box_muller(noise_bits(nk, k, static_cast<uint32_t>((j0 + 1) * QT + hc)), z1);
+        float z0[kPairH], z1[kPairH];
+        const int q0 = hc * (kPairH / 4);  // first noise block of the half
+#pragma unroll
+        for (int g = 0; g < kPairH / 4; ++g) {
+            if (4 * g < nc) {
+                box_muller(noise_bits(nk, k, static_cast<uint32_t>(j0 * QT + q0 + g)), z0 + 4 * g);
+                box_muller(noise_bits(nk, k, static_cast<uint32_t>((j0 + 1) * QT + q0 + g)),
+                           z1 + 4 * g);
+            }
+        }
 #pragma unroll
         for (int s = 0; s < kPairH; ++s) {
             if (s < nc) {
@@ -298,6 +306,8 @@ __global__ void __launch_bounds__(256, kSmemSpheres ? 2 : 0)
             p.S[k] = S;
         }
     }
+    // Every role passes the group's last barrier (the cost warp passed it
+    // above, before reading the noise warps' sums) before the block-wide tail.
     if (role != 3) group_sync(bar_id, 4 * kWarp);
     block_weight_tail(p, S, k_out, s_red, kWarp * ngroups);
 }

@@ -53,18 +53,8 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[a][i] = 0.f;
 
-    for (int idx = i_begin + threadIdx.x; idx < i_end; idx += blockDim.x) {
-        int k;
-        float w;
-        if (list) {
-            k = __ldcg(p.nz + idx);
-            w = __ldcg(p.w + idx);
-        } else {
-            k = idx;
-            const float S = p.S[k];
-            w = valid && is_finite(S) ? expf(-(S - rho) / p.lambda) / eta : 0.f;
-            if (w == 0.f) continue;
-        }
+    // add w_k eps_k of sample k to the QB Philox blocks of this tile
+    auto accumulate = [&](int k, float w) {
 #pragma unroll
         for (int a = 0; a < QB; ++a) {
             const int q = q0 + a;
@@ -74,6 +64,32 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
                 const float sig = p.sigma[q / QT];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) acc[a][i] += w * (sig * z[i]);
+            }
+        }
+    };
+    if (list) {
+        for (int idx = i_begin + threadIdx.x; idx < i_end; idx += blockDim.x)
+            accumulate(__ldcg(p.nz + idx), __ldcg(p.w + idx));
+    } else {
+        // every sample of the chunk: the weights of eight samples per thread
+        // at a time (their cost loads in flight together), then the noise of
+        // the non-zero ones only
+        constexpr int kBatch = 8;
+        auto weight = [&](float S) {
+            return valid && is_finite(S) ? expf(-(S - rho) / p.lambda) / eta : 0.f;
+        };
+        for (int base = i_begin + threadIdx.x; base < i_end; base += kBatch * blockDim.x) {
+            unsigned mask = 0u;
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int k = base + u * blockDim.x;
+                if (k < i_end && weight(p.S[k]) != 0.f) mask |= 1u << u;
+            }
+            while (mask) {
+                const int u = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const int k = base + u * blockDim.x;
+                accumulate(k, weight(p.S[k]));
             }
         }
     }
