@@ -221,39 +221,63 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def time_steps(fn, steps, warmup=3):
-    """Mean milliseconds of fn() over `steps` calls (CUDA events, current stream)."""
+def time_steps_flushed(fn, steps, flush, warmup=3):
+    """Mean milliseconds of fn() with the L2 flushed before each call (CUDA
+    events around each call on the current stream)."""
     import torch
     for _ in range(warmup):
         fn()
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     torch.cuda.synchronize()
-    s = torch.cuda.Event(enable_timing=True)
-    e = torch.cuda.Event(enable_timing=True)
-    s.record()
-    for _ in range(steps):
+    for i in range(steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
         fn()
-    e.record()
+        ends[i].record(stream)
     torch.cuda.synchronize()
-    return s.elapsed_time(e) / steps
+    return sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps
 
 
-def extensions(m, dev):
-    """The batched, differentiable and BF16-MLP forms on the same GPU."""
+def extensions(m, dev, peak_tflops, bf16_peak):
+    """The batched, differentiable and BF16-MLP forms on the same GPU, and
+    the quadrotor on a K sweep (where the FP32 roofline fraction is the
+    meaningful figure)."""
     import torch
     out = {}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     # batched: 256 instances, cart-pole and quadrotor, uneven K and T
     probs = W.batched()
     b = m.MPPIBatch(probs)
-    ms = time_steps(b.step, 20)
+    ms = time_steps_flushed(b.step, 20, flush)
     lat = b.latency_ms()
     rs = sum(p["K"] * p["T"] for p in probs)
+    flops = sum(p["K"] * p["T"] * FLOPS_PER_ROLLOUT_STEP[
+        "quadrotor" if p["dyn_kind"] == W.DYN_QUADROTOR else "cartpole"] for p in probs)
+    tflops = flops / (ms * 1e-3) / 1e12
     out["batched"] = {"workload": "256 instances (128 cart-pole, 128 quadrotor), K in "
                                   "{256..8192}, T in {50..200}, one graph launch per step",
                       "rollout_steps_per_s": rs / (ms * 1e-3), "ms_per_step": ms,
                       "instance_latency_ms": {"p50": float(np.percentile(lat, 50)),
                                               "p99": float(np.percentile(lat, 99))},
-                      "block_threads": b.info()["block_threads"]}
+                      "block_threads": b.info()["block_threads"],
+                      "achieved_tflops": tflops, "fp32_roofline_frac": tflops / peak_tflops}
     b.close()
+    # quadrotor K sweep (configuration 1 with more samples)
+    sweep = []
+    for K in (32768, 131072, 524288):
+        p = W.quadrotor(K=K)
+        c = m.MPPI.from_problem(p)
+        x0 = torch.tensor(p["x0"], dtype=torch.float32, device=dev)
+        u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device=dev)
+        un = torch.empty_like(u)
+        ms_k = time_steps_flushed(lambda: c.step_into(x0, u, un), 10, flush)
+        c.close()
+        tf = QUAD_FLOPS_PER_ROLLOUT_STEP * K * p["T"] / (ms_k * 1e-3) / 1e12
+        sweep.append({"K": K, "ms_per_step": ms_k, "rollout_steps_per_s": K * p["T"] / (ms_k * 1e-3),
+                      "achieved_tflops": tf, "fp32_roofline_frac": tf / peak_tflops})
+    out["quadrotor_k_sweep"] = sweep
     # differentiable: cart-pole K=4096, T=100, forward + adjoint backward
     p = W.differentiable()
     ctl = m.MPPI.from_problem(p)
@@ -267,8 +291,8 @@ def extensions(m, dev):
         ctl.step_into(x0, u, un)
         torch.mul(torch.sub(un, tgt), 2.0, out=gbuf)
         ctl.backward(gbuf)
-    ms_f = time_steps(lambda: ctl.step_into(x0, u, un), 20)
-    ms_fb = time_steps(fwd_bwd, 20)
+    ms_f = time_steps_flushed(lambda: ctl.step_into(x0, u, un), 20, flush)
+    ms_fb = time_steps_flushed(fwd_bwd, 20, flush)
     out["differentiable"] = {"workload": "cart-pole K=4096 T=100, loss ||u_new - u_target||^2, "
                                          "grads w.r.t. Q(4), R, l, m_c",
                              "forward_ms": ms_f, "forward_backward_ms": ms_fb,
@@ -282,13 +306,14 @@ def extensions(m, dev):
     res = {}
     for name, prec in (("bf16", m.MPPI_PREC_BF16_MLP), ("fp32", m.MPPI_PREC_FP32)):
         c = m.MPPI.from_problem(p, precision=prec)
-        res[name] = time_steps(lambda: c.step_into(x0, u, un), 10)
+        res[name] = time_steps_flushed(lambda: c.step_into(x0, u, un), 10, flush)
         c.close()
+    mlp_tflops = 2 * (6 * 64 + 64 * 64 + 64 * 4) * p["K"] * p["T"] / (res["bf16"] * 1e-3) / 1e12
     out["bf16_mlp"] = {"workload": "bicycle + MLP 6-64-64-4, K=16384 T=100, costmap 512x512",
                        "ms_per_step": res["bf16"], "fp32_ms_per_step": res["fp32"],
                        "rollout_steps_per_s": p["K"] * p["T"] / (res["bf16"] * 1e-3),
-                       "mlp_tflops": 2 * (6 * 64 + 64 * 64 + 64 * 4) * p["K"] * p["T"]
-                       / (res["bf16"] * 1e-3) / 1e12}
+                       "mlp_tflops": mlp_tflops,
+                       "bf16_tensor_frac": mlp_tflops / bf16_peak if bf16_peak else None}
     return out
 
 
@@ -442,7 +467,7 @@ def main():
         "clocks": clk,
     }
     if world == 1 and not args.no_extensions and args.workload == "quadrotor":
-        line["extensions"] = extensions(m, dev)
+        line["extensions"] = extensions(m, dev, peak_tflops, measured_peaks().get("bf16_tflops"))
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
     print(json.dumps(line), flush=True)

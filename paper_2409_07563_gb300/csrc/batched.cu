@@ -4,7 +4,9 @@
 // Kernel A (rollout): a grid of one or a few blocks per SM pulls work items
 // (instance, tile of samples) from an atomic head over a list sorted by
 // estimated cost (longest first).  Cart-pole tiles run one sample per
-// thread, quadrotor tiles four lanes per sample (quad_group.cuh).  Each tile
+// thread; quadrotor tiles run one sample per thread on four warp roles per 32
+// samples (quad_pair.cuh) when the block has 128 or 256 threads, else four
+// lanes per sample (quad_group.cuh).  Each tile
 // leaves (rho_b, eta_b, eta2_b); the last tile of an instance to finish
 // (per-instance ticket, nobody waits) merges its instance's partials into
 // rho, eta, F, ESS (Eq. 17-18, Eq. 4), writes the weights and an
@@ -29,6 +31,7 @@
 #include "models.cuh"
 #include "mppi_internal.h"
 #include "quad_group.cuh"
+#include "quad_pair.cuh"
 #include "sample_rollout.cuh"
 
 namespace mppi {
@@ -37,6 +40,15 @@ namespace {
 enum { kKindCartpole = 0, kKindQuad = 1 };
 constexpr int kBatchQb = 2;    // Philox blocks per update item
 constexpr int kBatchRed = 64;  // reduction scratch floats
+// shared memory of the quadrotor warp groups: spheres (kPairSpheres float4)
+// then kPairGroupFloats per group of four warps
+constexpr int kBatchPairFixed = 4 * kPairSpheres;
+static_assert(sizeof(QuadPairConst) <= sizeof(float) * kQuadSmemCostFloats,
+              "the cost slot holds a QuadPairConst");
+
+int batch_pair_floats(int threads) {
+    return threads >= 128 ? kBatchPairFixed + (threads / 128) * kPairGroupFloats : 0;
+}
 
 struct DevInst {
     int kind, K, T, nu, n_tiles, q_tiles, obstacles;
@@ -141,9 +153,12 @@ __global__ void __launch_bounds__(256) batch_rollout_kernel(const DevInst *insts
     float *s_cost = smem + smem_u;
     float *s_dyn = s_cost + smem_cost;
     float *s_red = s_dyn + 8;
+    float4 *s_obs = reinterpret_cast<float4 *>(s_red + kBatchRed);  // kPairSpheres float4
+    float *s_groups = s_red + kBatchRed + kBatchPairFixed;
     __shared__ int s_item;
     __shared__ bool s_last;
     const int tid = threadIdx.x, nt = blockDim.x;
+    const bool pair_roles = nt % 128 == 0;  // quadrotor tiles on warp roles
     if (blockIdx.x == 0 && tid == 0) *t_start = global_ns();
     for (;;) {
         if (tid == 0) s_item = static_cast<int>(atomicAdd(head, 1u));
@@ -153,13 +168,24 @@ __global__ void __launch_bounds__(256) batch_rollout_kernel(const DevInst *insts
         const Item item = items[it];
         const DevInst &I = insts[item.inst];
         for (int i = tid; i < I.T * I.nu; i += nt) s_u[i] = I.u_nom[i];
+        QuadPairConst *s_const = reinterpret_cast<QuadPairConst *>(s_cost);
         if (I.kind == kKindCartpole) {
             CartpoleDyn::prepare(I.dyn, s_dyn, tid, nt);
             QuadraticCost<4, 1>::prepare(I.cost, s_cost, tid, nt);
+        } else if (pair_roles) {
+            QuadrotorDyn::prepare(I.dyn, s_dyn, tid, nt);
+            pair_const_from_raw(I.cost, I.obstacles != 0, s_const, tid, nt);
         } else {
             quad_prepare_cost(I.cost, I.obstacles != 0, s_cost, tid, nt);
         }
         __syncthreads();
+        if (I.kind != kKindCartpole && pair_roles) {
+            for (int j = tid; j < kPairSpheres / 2; j += nt) {
+                s_obs[2 * j] = s_const->sa[j];
+                s_obs[2 * j + 1] = s_const->sb[j];
+            }
+            __syncthreads();
+        }
         const NoiseKey nk = make_noise_key(I.seed, *I.counter);
         float S = __int_as_float(0x7f800000);
         if (I.kind == kKindCartpole) {
@@ -168,6 +194,21 @@ __global__ void __launch_bounds__(256) batch_rollout_kernel(const DevInst *insts
                                CostCtx{nullptr, 0, 0}, nk};
             if (k < I.K) {
                 S = generic_sample_cost<CartpoleDyn, QuadraticCost<4, 1>>(a, static_cast<uint32_t>(k));
+                I.S[k] = S;
+            }
+        } else if (pair_roles) {
+            const int G = nt / 128, warp = tid / kWarp, lane = tid % kWarp;
+            const int role = warp / G, group = warp % G;
+            const PairArgs a{I.T, I.dt, I.lam_beta, I.sigma, I.ivar, I.x0, s_u, s_dyn, nk};
+            const uint32_t first_k = static_cast<uint32_t>(item.tile * (nt / 4) + group * kWarp);
+            float *sg = s_groups + group * kPairGroupFloats;
+            const float tot =
+                I.obstacles
+                    ? pair_group_cost<true, true>(a, *s_const, s_obs, sg, first_k, role, group, lane)
+                    : pair_group_cost<false, true>(a, *s_const, s_obs, sg, first_k, role, group, lane);
+            const int k = static_cast<int>(first_k) + lane;
+            if (role == 3 && k < I.K) {
+                S = tot;
                 I.S[k] = S;
             }
         } else {
@@ -353,7 +394,8 @@ cudaError_t upload_plan(mppi_batch &b, int threads) {
     e = cudaMemcpy(b.dev, b.dev_h.data(), b.n * sizeof(DevInst), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     b.threads = threads;
-    b.smem_bytes = sizeof(float) * static_cast<size_t>(b.smem_u + b.smem_cost + 8 + kBatchRed);
+    b.smem_bytes = sizeof(float) * static_cast<size_t>(b.smem_u + b.smem_cost + 8 + kBatchRed +
+                                                       batch_pair_floats(threads));
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_rollout_kernel, threads,
                                                       b.smem_bytes);
@@ -606,7 +648,8 @@ mppi_status mppi_batch_create(int n, const mppi_instance_desc *desc, const mppi_
     b->smem_cost = mppi::round_up4(max_cost);
     if (e == cudaSuccess) {
         const size_t smem =
-            sizeof(float) * static_cast<size_t>(b->smem_u + b->smem_cost + 8 + mppi::kBatchRed);
+            sizeof(float) * static_cast<size_t>(b->smem_u + b->smem_cost + 8 + mppi::kBatchRed +
+                                                 mppi::batch_pair_floats(256));
         e = cudaFuncSetAttribute(mppi::batch_rollout_kernel,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     }

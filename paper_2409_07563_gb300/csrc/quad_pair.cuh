@@ -1,0 +1,309 @@
+// quad_pair.cuh -- the quadrotor rollout of one group of 32 samples by four
+// warp roles (steps a1-a3), shared by the single-instance kernel
+// (rollout_quad_pair.cu) and the batched kernel (batched.cu).  The roles and
+// the ring they exchange through are described in rollout_quad_pair.cu.
+#pragma once
+
+#include "device_common.cuh"
+#include "models.cuh"
+
+namespace mppi {
+
+constexpr int kPairSpheres = 32;  // padded sphere count of the crash test
+
+// Cost constants of the quadrotor workload: a kernel parameter (constant
+// bank) in the single-instance kernel, a shared-memory copy in the batched one.
+struct QuadPairConst {
+    float Q[13], goal[13], R[4];
+    float s_term, c_crash;
+    // sphere pairs (2j, 2j+1): a = (cx, cx', cy, cy'), b = (cz, cz', -r^2, -r'^2)
+    float4 sa[kPairSpheres / 2], sb[kPairSpheres / 2];
+};
+
+constexpr int kPairH = 4;  // steps per ring half (whole Philox blocks of four steps)
+static_assert(kPairH % 4 == 0, "a ring half holds whole noise blocks");
+constexpr int kRingXPair = 2 * kPairH * 4 * kWarp;  // float4: [half][step][group][lane]
+constexpr int kRingVPair = 2 * kPairH * kWarp;      // float4: [half][step][lane]
+
+__device__ __forceinline__ void group_sync(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// fma(dz,dz, fma(dy,dy, fma(dx,dx, -r^2))) < 0 for any sphere, with
+// dx = fl(px - cx): one rounding per operation, two spheres per instruction.
+// The sphere pairs come from the kernel parameter (the compiler keeps them in
+// registers across the steps) or, for the low-register build, from shared
+// memory (obs2: sa[j] at 2j, sb[j] at 2j + 1).
+__device__ __forceinline__ float4 lds_v4_each_time(const float4 *a) {
+    float4 r;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "r"(static_cast<unsigned>(__cvta_generic_to_shared(a))));
+    return r;
+}
+
+template <bool kSmemSpheres>
+__device__ __forceinline__ bool crash_any(const QuadPairConst &c, const float4 *obs2, float px,
+                                          float py, float pz) {
+    const unsigned long long X = pack2(px, px), Y = pack2(py, py), Z = pack2(pz, pz);
+    bool hit = false;
+#pragma unroll
+    for (int j = 0; j < kPairSpheres / 2; ++j) {
+        // (a volatile load per step: otherwise the loop-invariant loads are
+        // hoisted into 128 registers, which is what this build avoids)
+        const float4 a = kSmemSpheres ? lds_v4_each_time(obs2 + 2 * j) : c.sa[j];
+        const float4 b = kSmemSpheres ? lds_v4_each_time(obs2 + 2 * j + 1) : c.sb[j];
+        const unsigned long long dx = sub2(X, pack2(a.x, a.y));
+        const unsigned long long dy = sub2(Y, pack2(a.z, a.w));
+        const unsigned long long dz = sub2(Z, pack2(b.x, b.y));
+        unsigned long long m = fma2(dx, dx, pack2(b.z, b.w));
+        m = fma2(dy, dy, m);
+        m = fma2(dz, dz, m);
+        float m0, m1;
+        unpack2(m, m0, m1);
+        hit |= (m0 < 0.0f) | (m1 < 0.0f);
+    }
+    return hit;
+}
+
+__device__ __forceinline__ float quad_state_cost(const QuadPairConst &c, const float y[13]) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 13; ++i) {
+        const float d = y[i] - c.goal[i];
+        s += c.Q[i] * d * d;
+    }
+    return s;
+}
+
+// RK4 step of the quadrotor (QuadrotorDyn::deriv, control held over the
+// step), then q <- q / |q| with the reciprocal square root.
+__device__ __forceinline__ void quad_rk4(float x[13], const float v[4], const float *P, float dt) {
+    float k[13], acc[13], tmp[13];
+    const float h = 0.5f * dt;
+    QuadrotorDyn::deriv(x, v, P, k);
+#pragma unroll
+    for (int i = 0; i < 13; ++i) {
+        acc[i] = k[i];
+        tmp[i] = x[i] + h * k[i];
+    }
+    QuadrotorDyn::deriv(tmp, v, P, k);
+#pragma unroll
+    for (int i = 0; i < 13; ++i) {
+        acc[i] += 2.0f * k[i];
+        tmp[i] = x[i] + h * k[i];
+    }
+    QuadrotorDyn::deriv(tmp, v, P, k);
+#pragma unroll
+    for (int i = 0; i < 13; ++i) {
+        acc[i] += 2.0f * k[i];
+        tmp[i] = x[i] + dt * k[i];
+    }
+    QuadrotorDyn::deriv(tmp, v, P, k);
+    const float d6 = dt / 6.0f;
+#pragma unroll
+    for (int i = 0; i < 13; ++i) x[i] += d6 * (acc[i] + k[i]);
+    const float inv = rsqrtf((x[6] * x[6] + x[7] * x[7]) + (x[8] * x[8] + x[9] * x[9]));
+#pragma unroll
+    for (int i = 6; i < 10; ++i) x[i] *= inv;
+}
+
+// Inputs of one group rollout.
+struct PairArgs {
+    int T;
+    float dt, lam_beta;
+    const float *sigma, *ivar;  // four channels
+    const float *x0;            // 13 states, global
+    const float *s_u;           // 4 T nominal controls, shared memory
+    const float *s_dyn;         // QuadrotorDyn parameters, shared memory
+    NoiseKey nk;
+};
+
+// Shared memory of one group: the state ring, the control ring and the noise
+// warps' partial sums.
+constexpr int kPairGroupFloats = 4 * (kRingXPair + kRingVPair) + 4 * kWarp;
+
+// Dynamics warp.
+__device__ __forceinline__ void pair_dynamics(const PairArgs &p, const float4 *ring_v,
+                                              float4 *ring_x, int lane, int nh, int bar_id) {
+    const int bar_threads = 4 * kWarp;
+    const int T = p.T;
+    float x[13];
+#pragma unroll
+    for (int i = 0; i < 13; ++i) x[i] = p.x0[i];
+    group_sync(bar_id, bar_threads);  // controls of half 0 are in the ring
+    for (int hh = 0; hh < nh; ++hh) {
+        const float4 *vb = ring_v + (hh & 1) * kPairH * kWarp;
+        float4 *xb = ring_x + (hh & 1) * kPairH * 4 * kWarp;
+        const int ns = min(kPairH, T - hh * kPairH);
+        float4 vv = vb[lane];
+#pragma unroll 1
+        for (int s = 0; s < ns; ++s) {
+            const float4 vn = vb[min(s + 1, kPairH - 1) * kWarp + lane];
+            const float v[4] = {vv.x, vv.y, vv.z, vv.w};
+            quad_rk4(x, v, p.s_dyn, p.dt);
+            float4 *o = xb + s * 4 * kWarp + lane;
+            o[0] = make_float4(x[0], x[1], x[2], x[3]);
+            o[kWarp] = make_float4(x[4], x[5], x[6], x[7]);
+            o[2 * kWarp] = make_float4(x[8], x[9], x[10], x[11]);
+            o[3 * kWarp] = make_float4(x[12], 0.f, 0.f, 0.f);
+            vv = vn;
+        }
+        group_sync(bar_id, bar_threads);
+    }
+}
+
+// Noise warp for channels j0, j0 + 1: writes (v_j0, v_j0+1) of every step
+// into the ring and returns its compensated sum of
+// R_j v_j^2 + beta lambda (v_j - u_j / 2) u_j / sigma_j^2.
+__device__ __forceinline__ FloatPair pair_noise(const PairArgs &p, const QuadPairConst &c,
+                                                float4 *ring_v, uint32_t k, int j0, int lane,
+                                                int nh, int bar_id) {
+    const float *s_u = p.s_u;
+    const int T = p.T, QT = (T + 3) / 4;
+    const float lamb = p.lam_beta;
+    const float sg0 = p.sigma[j0], sg1 = p.sigma[j0 + 1];
+    const float iv0 = p.ivar[j0], iv1 = p.ivar[j0 + 1];
+    const float R0 = c.R[j0], R1 = c.R[j0 + 1];
+    const NoiseKey nk = p.nk;
+    CompSum J;
+    auto controls = [&](int hc) {
+        float2 *vb = reinterpret_cast<float2 *>(ring_v + (hc & 1) * kPairH * kWarp) + (j0 >> 1);
+        const int nc = min(kPairH, T - hc * kPairH);
+        float z0[kPairH], z1[kPairH];
+        const int q0 = hc * (kPairH / 4);  // first noise block of the half
+#pragma unroll
+        for (int g = 0; g < kPairH / 4; ++g) {
+            if (4 * g < nc) {
+                box_muller(noise_bits(nk, k, static_cast<uint32_t>(j0 * QT + q0 + g)), z0 + 4 * g);
+                box_muller(noise_bits(nk, k, static_cast<uint32_t>((j0 + 1) * QT + q0 + g)),
+                           z1 + 4 * g);
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < kPairH; ++s) {
+            if (s < nc) {
+                const int t = hc * kPairH + s;
+                const float2 u = reinterpret_cast<const float2 *>(s_u + 4 * t)[j0 >> 1];
+                const float v0 = u.x + sg0 * z0[s], v1 = u.y + sg1 * z1[s];
+                vb[2 * (s * kWarp + lane)] = make_float2(v0, v1);
+                const float is = (v0 - 0.5f * u.x) * (u.x * iv0) + (v1 - 0.5f * u.y) * (u.y * iv1);
+                J.add(R0 * v0 * v0 + R1 * v1 * v1 + lamb * is);
+            }
+        }
+    };
+    controls(0);
+    group_sync(bar_id, 4 * kWarp);
+    for (int hh = 0; hh < nh; ++hh) {
+        if (hh + 1 < nh) controls(hh + 1);
+        group_sync(bar_id, 4 * kWarp);
+    }
+    return FloatPair{J.s, J.c};
+}
+
+// Cost warp: state part of the running cost of every x_{t+1}, crash cost,
+// terminal cost.
+template <bool kObstacles, bool kSmemSpheres>
+__device__ __forceinline__ FloatPair pair_state_cost(const PairArgs &p, const QuadPairConst &c,
+                                                     const float4 *obs2, const float4 *ring_x,
+                                                     int lane, int nh, int bar_id) {
+    const int T = p.T;
+    CompSum J;
+    auto state = [&](const float4 *slot, int t) {
+        const float4 a = slot[0], b = slot[kWarp], d = slot[2 * kWarp], e = slot[3 * kWarp];
+        const float y[13] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, d.x, d.y, d.z, d.w, e.x};
+        const float cs = quad_state_cost(c, y);
+        float r = cs;
+        if (kObstacles && crash_any<kSmemSpheres>(c, obs2, y[0], y[1], y[2])) r += c.c_crash;
+        J.add(fmaf(t == T - 1 ? c.s_term : 0.f, cs, r));
+    };
+    auto states = [&](int hs) {
+        const float4 *xb = ring_x + (hs & 1) * kPairH * 4 * kWarp + lane;
+        const int nx = min(kPairH, T - hs * kPairH);
+        if (!kSmemSpheres && nx == kPairH) {  // straight-line steady state
+#pragma unroll
+            for (int s = 0; s < kPairH; ++s) state(xb + s * 4 * kWarp, hs * kPairH + s);
+            return;
+        }
+#pragma unroll 1
+        for (int s = 0; s < nx; ++s) state(xb + s * 4 * kWarp, hs * kPairH + s);
+    };
+    group_sync(bar_id, 4 * kWarp);
+    for (int hh = 0; hh < nh; ++hh) {
+        if (hh >= 1) states(hh - 1);
+        group_sync(bar_id, 4 * kWarp);
+    }
+    states(nh - 1);
+    return FloatPair{J.s, J.c};
+}
+
+// One group of 32 samples (first_k, ..., first_k + 31) on warps
+// (role * G + group) of the calling block, role 0 dynamics, 1-2 noise, 3 cost;
+// every thread of the block calls it.  s_group: kPairGroupFloats of shared
+// memory for this group; s_obs: the spheres in shared memory (kSmemSpheres).
+// Returns the trajectory cost in the cost warp's threads, +inf elsewhere.
+template <bool kObstacles, bool kSmemSpheres>
+__device__ __forceinline__ float pair_group_cost(const PairArgs &a, const QuadPairConst &c,
+                                                 const float4 *s_obs, float *s_group,
+                                                 uint32_t first_k, int role, int group,
+                                                 int lane) {
+    float4 *ring_x = reinterpret_cast<float4 *>(s_group);
+    float4 *ring_v = ring_x + kRingXPair;
+    FloatPair *s_part = reinterpret_cast<FloatPair *>(ring_v + kRingVPair);
+    const int nh = (a.T + kPairH - 1) / kPairH;
+    const int bar_id = 1 + group;
+    float S = __int_as_float(0x7f800000);
+    if (role == 0) {
+        pair_dynamics(a, ring_v, ring_x, lane, nh, bar_id);
+    } else if (role <= 2) {
+        s_part[(role - 1) * kWarp + lane] =
+            pair_noise(a, c, ring_v, first_k + lane, 2 * (role - 1), lane, nh, bar_id);
+    } else {
+        FloatPair tot = pair_state_cost<kObstacles, kSmemSpheres>(a, c, s_obs, ring_x, lane, nh,
+                                                                 bar_id);
+        group_sync(bar_id, 4 * kWarp);  // the noise warps' sums are in place
+        tot = pair_add(tot, s_part[lane]);
+        tot = pair_add(tot, s_part[kWarp + lane]);
+        S = tot.hi + tot.lo;
+    }
+    // every role passes the group's last barrier (the cost warp passed it
+    // above, before reading the noise warps' sums)
+    if (role != 3) group_sync(bar_id, 4 * kWarp);
+    return S;
+}
+
+// Device-side copy of the cost constants from the raw parameter block
+// (QuadObstacleCost layout: Q(13), R(4), goal(13), s, n_obs, c_crash, then
+// (cx, cy, cz, r) per sphere); padded spheres are never hit.
+__device__ inline void pair_const_from_raw(const float *raw, bool obstacles, QuadPairConst *c,
+                                           int tid, int nt) {
+    for (int i = tid; i < 13; i += nt) {
+        c->Q[i] = raw[i];
+        c->goal[i] = raw[17 + i];
+    }
+    for (int j = tid; j < 4; j += nt) c->R[j] = raw[13 + j];
+    if (tid == 0) {
+        c->s_term = raw[30];
+        c->c_crash = obstacles ? raw[32] : 0.f;
+    }
+    const int n = obstacles ? static_cast<int>(raw[31]) : 0;
+    for (int j = tid; j < kPairSpheres / 2; j += nt) {
+        float q[2][4];
+        for (int h = 0; h < 2; ++h) {
+            const int i = 2 * j + h;
+            if (i < n) {
+                q[h][0] = raw[33 + 4 * i];
+                q[h][1] = raw[33 + 4 * i + 1];
+                q[h][2] = raw[33 + 4 * i + 2];
+                q[h][3] = -__fmul_rn(raw[33 + 4 * i + 3], raw[33 + 4 * i + 3]);
+            } else {
+                q[h][0] = q[h][1] = q[h][2] = 0.f;
+                q[h][3] = 3.0e38f;
+            }
+        }
+        c->sa[j] = make_float4(q[0][0], q[1][0], q[0][1], q[1][1]);
+        c->sb[j] = make_float4(q[0][2], q[1][2], q[0][3], q[1][3]);
+    }
+}
+
+}  // namespace mppi
