@@ -71,6 +71,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, device, world):
+    """The maximum of x over all ranks (every rank gets it); x itself when
+    world == 1.  The job is as slow as its slowest replica."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(rollout_steps_per_rank, world, ms_max):
+    """Whole-job rollout-steps/s: every rank processes its own replica of the
+    workload (weak scaling), and the job takes the slowest rank's time."""
+    return world * rollout_steps_per_rank / (ms_max * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
 
@@ -397,13 +415,9 @@ def main():
     prof = ctl.profile_read()
     clk = clocks.stop()
     per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = sum(per_step) / len(per_step)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(per_step) / len(per_step), dev, world)
     rollout_steps = p["K"] * p["T"]
-    value = world * rollout_steps / (ms * 1e-3)
+    value = job_throughput(rollout_steps, world, ms)
 
     # ---- end to end through the host-buffer entry point -----------------------
     x0_h = torch.tensor(p["x0"], dtype=torch.float32).pin_memory()
@@ -418,11 +432,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ctl.step_host_ptr(x0_h.data_ptr(), u_h.data_ptr(), un_h.data_ptr(), st_h.data_ptr())
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps, dev, world)
     h2d = (p["nx"] + p["T"] * p["nu"]) * 4
     d2h = (p["T"] * p["nu"] + 4) * 4
 
@@ -460,7 +470,7 @@ def main():
         "latency_ms": {"p50": float(np.percentile(per_step, 50)),
                        "p99": float(np.percentile(per_step, 99)),
                        "region_s": region_s},
-        "e2e": {"value": world * rollout_steps / (e2e_ms * 1e-3), "unit": UNIT,
+        "e2e": {"value": job_throughput(rollout_steps, world, e2e_ms), "unit": UNIT,
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": roll_n + upd_n,
         "roofline": roofline,

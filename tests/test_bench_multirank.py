@@ -1,0 +1,71 @@
+"""Host-side logic of bench.py's multi-rank path, on CPU.
+
+Multi-GPU runs are independent replicas (weak scaling): the only exchange is
+the maximum of the per-rank step times.  These tests run that exchange with
+two gloo ranks, and the reference arm under torchrun with two ranks (rank 0
+alone prints its line; the other exits 0)."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_path):
+    import torch
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = bench.max_over_ranks(1.5 + rank, torch.device("cpu"), world)
+        value = bench.job_throughput(1000, world, ms)
+        with open(f"{out_path}.{rank}", "w") as f:
+            json.dump({"ms": ms, "value": value}, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_job_throughput_gloo(tmp_path):
+    import torch.multiprocessing as mp
+    world = 2
+    out = str(tmp_path / "r")
+    mp.start_processes(_rank_main, args=(world, _free_port(), out), nprocs=world,
+                       start_method="spawn")
+    for r in range(world):
+        with open(f"{out}.{r}") as f:
+            d = json.load(f)
+        assert d["ms"] == 2.5                      # the slowest rank's time, on every rank
+        assert d["value"] == pytest.approx(2 * 1000 / 2.5e-3)
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.max_over_ranks(3.25, None, 1) == 3.25
+    assert bench.job_throughput(100, 1, 2.0) == pytest.approx(100 / 2e-3)
+
+
+def test_reference_arm_under_torchrun_prints_one_line():
+    port = _free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl",
+           "reference", "--workload", "cartpole", "--K", "256", "--steps", "2", "--warmup", "3"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
