@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) rollout_kernel(const StepParams p) {
         p.S[k] = S;
     }
 
-    block_weight_tail(p, S, k < p.K ? k : -1, s_red, blockDim.x);
+    block_weight_tail(p, S, k < p.K ? k : -1, s_red, blockDim.x, s_u);
 }
 
 template <class Dyn, class Cost>

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256) bicycle_mlp_bf16_kernel(const StepParams 
         S = J.value();
         p.S[k] = S;
     }
-    block_weight_tail(p, S, active ? k : -1, s_red, blockDim.x);
+    block_weight_tail(p, S, active ? k : -1, s_red, blockDim.x, s_u);
 }
 
 }  // namespace

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) quad_group_kernel(const StepParams p) {
         S = tot;
         p.S[k] = S;
     }
-    block_weight_tail(p, S, (k < p.K && r == 0) ? k : -1, s_red, blockDim.x / 4);
+    block_weight_tail(p, S, (k < p.K && r == 0) ? k : -1, s_red, blockDim.x / 4, s_u);
 }
 
 }  // namespace

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256, kSmemSpheres ? 2 : 0)
         k_out = k;
         p.S[k] = S;
     }
-    block_weight_tail(p, S, k_out, s_red, kWarp * ngroups);
+    block_weight_tail(p, S, k_out, s_red, kWarp * ngroups, s_u);
 }
 
 }  // namespace

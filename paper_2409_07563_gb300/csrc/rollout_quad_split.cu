@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(512) quad_split_kernel(const StepParams p) {
             p.S[k] = S;
         }
     }
-    block_weight_tail(p, S, k_out, s_red, 8 * npairs);
+    block_weight_tail(p, S, k_out, s_red, 8 * npairs, s_u);
 }
 
 }  // namespace

@@ -53,7 +53,7 @@ __device__ __forceinline__ float key_float(unsigned int k) {
 // in registers.  Larger grids walk contiguous block ranges per thread.
 constexpr int kMaxFinalizeThreads = 512;
 __device__ inline void finalize_weights(const StepParams &p, int nblocks, int cand_stride,
-                                        float *red) {
+                                        float *red, const float *s_unom) {
     __shared__ int s_off[kMaxFinalizeThreads + 1];  // candidate offset of each block
     __shared__ int s_nzk[kInlineUpdateCalls];       // a short non-zero list for the inline update
     __shared__ float s_nzw[kInlineUpdateCalls];
@@ -207,6 +207,7 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, int ca
     const bool inline_update = list_mode && nnz * per_thread <= kInlineUpdateCalls;
     if (inline_update) {
         const NoiseKey nk = make_noise_key(p.seed, step);
+        const float *un = s_unom ? s_unom : p.u_nom;  // the block's shared copy when it has one
         for (int q = tid; q < Q; q += nt) {
             const int j = q / QT, t0 = 4 * (q % QT);
             const float sig = p.sigma[j];
@@ -223,7 +224,7 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, int ca
             for (int i = 0; i < 4; ++i) {
                 if (t0 + i < p.T) {
                     const int o = (t0 + i) * p.nu + j;
-                    p.u_new[o] = p.u_nom[o] + acc[i];
+                    p.u_new[o] = un[o] + acc[i];
                 }
             }
         }
@@ -258,13 +259,14 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, int ca
 // Called by every thread of the block after its samples are done; S is this
 // thread's trajectory cost (+inf for threads that carry no sample) and k its
 // sample index (or -1); cand_stride bounds the samples a block carries (its
-// candidate slots start at blockIdx.x * cand_stride).  The block folds its minimum into a running global
+// candidate slots start at blockIdx.x * cand_stride); s_unom is the block's
+// shared copy of u_nom for the inline update, or null.  The block folds its minimum into a running global
 // minimum m (atomicMin; m >= the final minimum) and keeps as candidates its
 // samples with S - m < 110 lambda -- every other sample has weight exactly
 // zero.  It leaves (rho_b, eta_b, eta2_b, n_cand) and its candidates; the last
 // block to finish (atomic ticket; nobody waits) merges them (Eq. 17-18, Eq. 4).
 __device__ inline void block_weight_tail(const StepParams &p, float S, int k, float *s_red,
-                                         int cand_stride) {
+                                         int cand_stride, const float *s_unom) {
     const float Sf = is_finite(S) ? S : __int_as_float(0x7f800000);
     if (k >= 0 && p.costs_out) p.costs_out[k] = S;
     const float rho_b = block_min(Sf, s_red);
@@ -291,6 +293,9 @@ __device__ inline void block_weight_tail(const StepParams &p, float S, int k, fl
         reinterpret_cast<int2 *>(p.cand)[static_cast<size_t>(blockIdx.x) * cand_stride + slot] =
             make_int2(k, __float_as_int(Sf));
     __shared__ bool s_last;
+    // the barrier orders every thread's candidate write before thread 0's
+    // device-scope fence (cumulative), and so before the ticket
+    __syncthreads();
     if (threadIdx.x == 0) {
         p.partials[4 * blockIdx.x + 0] = rho_b;
         p.partials[4 * blockIdx.x + 1] = eta_b.hi + eta_b.lo;
@@ -303,7 +308,7 @@ __device__ inline void block_weight_tail(const StepParams &p, float S, int k, fl
     __syncthreads();
     if (s_last) {
         __threadfence();
-        finalize_weights(p, gridDim.x, cand_stride, s_red);
+        finalize_weights(p, gridDim.x, cand_stride, s_red, s_unom);
     }
     allow_successor_launch();
 }
