@@ -87,8 +87,16 @@ class MPPI:
                            float(lam), _fptr(self._sigma), ctypes.byref(opt), ctypes.byref(h))
         check(st, "mppi_create")
         self._h = h
+        self._stream_val = None  # the stream handle last given to mppi_set_stream
         self.K, self.T, self.nx, self.nu = int(K), int(T), int(nx), int(nu)
         self.lam = float(lam)
+
+    def _use_stream(self, L, stream):
+        """mppi_set_stream, skipped when the context already uses that stream."""
+        hs = _stream_handle(stream)
+        if hs.value != self._stream_val:
+            check(L.mppi_set_stream(self._h, hs), "mppi_set_stream", self._h)
+            self._stream_val = hs.value
 
     @classmethod
     def from_problem(cls, p: dict, **kw):
@@ -132,7 +140,7 @@ class MPPI:
         _check_tensor(weights, self.K, "weights")
         _check_tensor(stats, 4, "stats")
         _check_tensor(costs, self.K, "costs")
-        check(L.mppi_set_stream(self._h, _stream_handle(stream)), "mppi_set_stream", self._h)
+        self._use_stream(L, stream)
         st = L.mppi_step(self._h, _dptr(x0), _dptr(u_nom), _dptr(u_new), _dptr(weights),
                          _dptr(stats), _dptr(costs))
         check(st, "mppi_step", self._h)
@@ -160,7 +168,7 @@ class MPPI:
         u_nom = _f32(u_nom).reshape(-1)
         u_new = np.empty(self.T * self.nu, dtype=np.float32)
         stats = np.empty(4, dtype=np.float32)
-        check(L.mppi_set_stream(self._h, _stream_handle(stream)), "mppi_set_stream", self._h)
+        self._use_stream(L, stream)
         check(L.mppi_step_host(self._h, _fptr(x0), _fptr(u_nom), _fptr(u_new), _fptr(stats)),
               "mppi_step_host", self._h)
         return u_new.reshape(self.T, self.nu), stats
@@ -168,7 +176,7 @@ class MPPI:
     def step_host_ptr(self, x0_ptr, u_nom_ptr, u_new_ptr, stats_ptr=None, stream=None):
         """``mppi_step_host`` on raw host addresses (e.g. pinned torch tensors)."""
         L = load()
-        check(L.mppi_set_stream(self._h, _stream_handle(stream)), "mppi_set_stream", self._h)
+        self._use_stream(L, stream)
         fp = ctypes.POINTER(ctypes.c_float)
         st = L.mppi_step_host(self._h, ctypes.cast(x0_ptr, fp), ctypes.cast(u_nom_ptr, fp),
                               ctypes.cast(u_new_ptr, fp),
@@ -190,7 +198,7 @@ class MPPI:
         g = grad_u_new.reshape(-1).contiguous()
         _check_tensor(g, self.T * self.nu, "grad_u_new")
         out = torch.empty(7, device=g.device, dtype=torch.float32)
-        check(L.mppi_set_stream(self._h, _stream_handle(stream)), "mppi_set_stream", self._h)
+        self._use_stream(L, stream)
         check(L.mppi_step_backward(self._h, _dptr(g), _dptr(out)), "mppi_step_backward", self._h)
         return out
 

@@ -84,6 +84,7 @@ class ProfScope {
 void free_ctx(mppi_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->io_host) cudaFreeHost(c->io_host);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     void *ptrs[] = {c->d_dyn, c->d_cost, c->d_map, c->scr.S, c->scr.w, c->scr.nz, c->scr.cand,
                     c->scr.partials, c->scr.upartials,
@@ -441,24 +442,32 @@ mppi_status mppi_step_host(mppi_ctx *ctx, const float *x0_h, const float *u_nom_
     if (!ctx) return MPPI_ERR_INVALID_ARG;
     if (!x0_h || !u_nom_h || !u_new_h)
         return fail(ctx, MPPI_ERR_INVALID_ARG, "x0, u_nom and u_new must be host pointers");
-    const size_t TN = static_cast<size_t>(ctx->T) * ctx->nu;
-    float *d_x0 = ctx->scr.io, *d_u = d_x0 + ctx->nx, *d_un = d_u + TN, *d_st = d_un + TN;
+    const size_t TN = static_cast<size_t>(ctx->T) * ctx->nu, nx = static_cast<size_t>(ctx->nx);
+    // device staging [x0 | u_nom | u_new | stats] and its pinned host mirror:
+    // one copy in, one copy out per step
+    float *d_x0 = ctx->scr.io, *d_u = d_x0 + nx, *d_un = d_u + TN, *d_st = d_un + TN;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(d_x0, x0_h, ctx->nx * sizeof(float), cudaMemcpyHostToDevice,
-                             ctx->stream)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d_u, u_nom_h, TN * sizeof(float), cudaMemcpyHostToDevice,
+    if (!ctx->io_host &&
+        (e = cudaMallocHost(reinterpret_cast<void **>(&ctx->io_host),
+                            sizeof(float) * (nx + 2 * TN + 4))) != cudaSuccess) {
+        ctx->io_host = nullptr;
+        return cuda_fail(ctx, e, "pinned staging allocation");
+    }
+    float *h = ctx->io_host;
+    std::memcpy(h, x0_h, nx * sizeof(float));
+    std::memcpy(h + nx, u_nom_h, TN * sizeof(float));
+    if ((e = cudaMemcpyAsync(d_x0, h, (nx + TN) * sizeof(float), cudaMemcpyHostToDevice,
                              ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "host-to-device copy");
-    mppi_status st = mppi_step(ctx, d_x0, d_u, d_un, nullptr, stats_h ? d_st : nullptr, nullptr);
+    mppi_status st = mppi_step(ctx, d_x0, d_u, d_un, nullptr, d_st, nullptr);
     if (st != MPPI_OK) return st;
-    if ((e = cudaMemcpyAsync(u_new_h, d_un, TN * sizeof(float), cudaMemcpyDeviceToHost,
+    if ((e = cudaMemcpyAsync(h + nx + TN, d_un, (TN + 4) * sizeof(float), cudaMemcpyDeviceToHost,
                              ctx->stream)) != cudaSuccess)
-        return cuda_fail(ctx, e, "device-to-host copy");
-    if (stats_h && (e = cudaMemcpyAsync(stats_h, d_st, 4 * sizeof(float), cudaMemcpyDeviceToHost,
-                                        ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "device-to-host copy");
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "stream synchronize");
+    std::memcpy(u_new_h, h + nx + TN, TN * sizeof(float));
+    if (stats_h) std::memcpy(stats_h, h + nx + 2 * TN, 4 * sizeof(float));
     return MPPI_OK;
 }
 

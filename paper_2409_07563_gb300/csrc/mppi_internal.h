@@ -100,6 +100,7 @@ struct mppi_ctx {
     float *d_dyn = nullptr, *d_cost = nullptr, *d_map = nullptr;
     int map_h = 0, map_w = 0;
     mppi::Scratch scr;
+    float *io_host = nullptr;           // pinned mirror of scr.io for mppi_step_host (first use)
     mppi::LaunchPlan plan;
     cudaStream_t stream = nullptr;
     int device = 0, num_sms = 0;
