@@ -325,6 +325,30 @@ def test_in_place_update_and_host_entry(m):
     assert np.array_equal(u_host.reshape(-1), ref.cpu().numpy())
 
 
+@pytest.mark.parametrize("make", [lambda: W.quadrotor(K=1024, T=40, lam=200.0, beta=0),
+                                  lambda: W.cartpole(K=300, T=21, lam=20.0)])
+def test_host_entry_repeated_and_after_set_params(m, make):
+    # the host entry replays one captured sequence: new inputs every call,
+    # and new parameters after mppi_set_params, must reach the kernels
+    p = as_f32_problem(make())
+    ctl = m.MPPI.from_problem(p)
+    rng = np.random.default_rng(5)
+    for i in range(3):
+        if i == 2:
+            cp = p["cost_params"].copy()
+            cp[0] *= 3.0
+            ctl.set_params(cost_params=cp)
+        x0 = (p["x0"] + 0.01 * i).astype(np.float32)
+        un = (p["u_nom"] + 0.1 * rng.standard_normal(p["u_nom"].shape)).astype(np.float32)
+        ctl.counter = 7 + i
+        u_host, st_host = ctl.step_host(x0, un)
+        ctl.counter = 7 + i
+        d = ctl.step(torch.tensor(x0, device="cuda"), torch.tensor(un.reshape(-1), device="cuda"))
+        torch.cuda.synchronize()
+        assert np.array_equal(u_host.reshape(-1), d["u_new"].reshape(-1).cpu().numpy())
+        assert np.array_equal(st_host, d["stats"].cpu().numpy())
+
+
 def test_invalid_arguments_are_rejected(m):
     p = W.cartpole()
     with pytest.raises(m.MPPIError):
