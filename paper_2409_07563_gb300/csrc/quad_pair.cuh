@@ -76,30 +76,80 @@ __device__ __forceinline__ float quad_state_cost(const QuadPairConst &c, const f
     return s;
 }
 
-// RK4 step of the quadrotor (QuadrotorDyn::deriv, control held over the
-// step), then q <- q / |q| with the reciprocal square root.
-__device__ __forceinline__ void quad_rk4(float x[13], const float v[4], const float *P, float dt) {
+// Quadrotor constants held in registers by the dynamics warp.
+struct QuadDynRegs {
+    float inv_m, g;
+    float dJ[3];   // J_z - J_y, J_x - J_z, J_y - J_x: (omega x J omega)_a = dJ_a omega_b omega_c
+    float iJ[3];   // 1 / J_a
+};
+
+__device__ __forceinline__ QuadDynRegs quad_dyn_regs(const float *P) {  // QuadrotorDyn layout
+    QuadDynRegs r;
+    r.inv_m = P[0];
+    r.g = P[4];
+    r.dJ[0] = P[3] - P[2];
+    r.dJ[1] = P[1] - P[3];
+    r.dJ[2] = P[2] - P[1];
+    r.iJ[0] = P[5];
+    r.iJ[1] = P[6];
+    r.iJ[2] = P[7];
+    return r;
+}
+
+// The quadrotor model of QuadrotorDyn::deriv (p' = v, v' = R(q) e_z f/m - g e_z,
+// q' = q (x) (0, omega) / 2, omega' = J^-1 (tau - omega x J omega)) with the
+// operations regrouped: 2 f/m and omega/2 are exact power-of-two scalings
+// taken once, and for the diagonal J the gyroscopic term of axis a is
+// (J_c - J_b) omega_b omega_c (a, b, c cyclic).  Same function, other
+// rounding order (about 34 instead of 43 operations).
+__device__ __forceinline__ void quad_deriv_regs(const float x[13], float fm, float f2,
+                                                const float tau[3], const QuadDynRegs &d,
+                                                float xd[13]) {
+    const float qw = x[6], qx = x[7], qy = x[8], qz = x[9];
+    const float a = x[10], b = x[11], c = x[12];
+    xd[0] = x[3];
+    xd[1] = x[4];
+    xd[2] = x[5];
+    xd[3] = fmaf(qw, qy, qx * qz) * f2;
+    xd[4] = fmaf(-qw, qx, qy * qz) * f2;
+    xd[5] = fmaf(fmaf(-2.0f, fmaf(qy, qy, qx * qx), 1.0f), fm, -d.g);
+    const float ha = 0.5f * a, hb = 0.5f * b, hc = 0.5f * c;
+    xd[6] = fmaf(-qz, hc, fmaf(-qy, hb, -qx * ha));
+    xd[7] = fmaf(-qz, hb, fmaf(qy, hc, qw * ha));
+    xd[8] = fmaf(-qx, hc, fmaf(qz, ha, qw * hb));
+    xd[9] = fmaf(-qy, ha, fmaf(qx, hb, qw * hc));
+    xd[10] = fmaf(-d.dJ[0], b * c, tau[0]) * d.iJ[0];
+    xd[11] = fmaf(-d.dJ[1], a * c, tau[1]) * d.iJ[1];
+    xd[12] = fmaf(-d.dJ[2], a * b, tau[2]) * d.iJ[2];
+}
+
+// RK4 step of the quadrotor (control held over the step), then q <- q / |q|
+// with the reciprocal square root.
+__device__ __forceinline__ void quad_rk4(float x[13], const float v[4], const QuadDynRegs &d,
+                                         float dt) {
     float k[13], acc[13], tmp[13];
     const float h = 0.5f * dt;
-    QuadrotorDyn::deriv(x, v, P, k);
+    const float fm = v[0] * d.inv_m, f2 = 2.0f * fm;
+    const float tau[3] = {v[1], v[2], v[3]};
+    quad_deriv_regs(x, fm, f2, tau, d, k);
 #pragma unroll
     for (int i = 0; i < 13; ++i) {
         acc[i] = k[i];
         tmp[i] = x[i] + h * k[i];
     }
-    QuadrotorDyn::deriv(tmp, v, P, k);
+    quad_deriv_regs(tmp, fm, f2, tau, d, k);
 #pragma unroll
     for (int i = 0; i < 13; ++i) {
         acc[i] += 2.0f * k[i];
         tmp[i] = x[i] + h * k[i];
     }
-    QuadrotorDyn::deriv(tmp, v, P, k);
+    quad_deriv_regs(tmp, fm, f2, tau, d, k);
 #pragma unroll
     for (int i = 0; i < 13; ++i) {
         acc[i] += 2.0f * k[i];
         tmp[i] = x[i] + dt * k[i];
     }
-    QuadrotorDyn::deriv(tmp, v, P, k);
+    quad_deriv_regs(tmp, fm, f2, tau, d, k);
     const float d6 = dt / 6.0f;
 #pragma unroll
     for (int i = 0; i < 13; ++i) x[i] += d6 * (acc[i] + k[i]);
@@ -128,6 +178,7 @@ __device__ __forceinline__ void pair_dynamics(const PairArgs &p, const float4 *r
                                               float4 *ring_x, int lane, int nh, int bar_id) {
     const int bar_threads = 4 * kWarp;
     const int T = p.T;
+    const QuadDynRegs dyn = quad_dyn_regs(p.s_dyn);
     float x[13];
 #pragma unroll
     for (int i = 0; i < 13; ++i) x[i] = p.x0[i];
@@ -141,7 +192,7 @@ __device__ __forceinline__ void pair_dynamics(const PairArgs &p, const float4 *r
         for (int s = 0; s < ns; ++s) {
             const float4 vn = vb[min(s + 1, kPairH - 1) * kWarp + lane];
             const float v[4] = {vv.x, vv.y, vv.z, vv.w};
-            quad_rk4(x, v, p.s_dyn, p.dt);
+            quad_rk4(x, v, dyn, p.dt);
             float4 *o = xb + s * 4 * kWarp + lane;
             o[0] = make_float4(x[0], x[1], x[2], x[3]);
             o[kWarp] = make_float4(x[4], x[5], x[6], x[7]);
