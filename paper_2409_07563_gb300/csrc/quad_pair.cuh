@@ -123,36 +123,66 @@ __device__ __forceinline__ void quad_deriv_regs(const float x[13], float fm, flo
     xd[12] = fmaf(-d.dJ[2], a * b, tau[2]) * d.iJ[2];
 }
 
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
 // RK4 step of the quadrotor (control held over the step), then q <- q / |q|
-// with the reciprocal square root.
+// with the reciprocal square root.  The stage combinations run on pairs of
+// state components (f32x2: rounded per element exactly like the scalar
+// fmaf), the derivative on scalars.
 __device__ __forceinline__ void quad_rk4(float x[13], const float v[4], const QuadDynRegs &d,
                                          float dt) {
-    float k[13], acc[13], tmp[13];
-    const float h = 0.5f * dt;
+    constexpr int NP = 7;  // state pairs (x[12], 0)
+    float k[14], tmp[14];
+    unsigned long long X[NP], A[NP], Kp[NP];
+    const float h = 0.5f * dt, d6 = dt / 6.0f;
+    const unsigned long long H2 = pack2(h, h), DT2 = pack2(dt, dt), D62 = pack2(d6, d6);
+    const unsigned long long TWO2 = pack2(2.0f, 2.0f);
     const float fm = v[0] * d.inv_m, f2 = 2.0f * fm;
     const float tau[3] = {v[1], v[2], v[3]};
-    quad_deriv_regs(x, fm, f2, tau, d, k);
 #pragma unroll
-    for (int i = 0; i < 13; ++i) {
-        acc[i] = k[i];
-        tmp[i] = x[i] + h * k[i];
+    for (int i = 0; i < NP; ++i) X[i] = pack2(x[2 * i], 2 * i + 1 < 13 ? x[2 * i + 1] : 0.f);
+    auto stage = [&](const float *in) {
+        quad_deriv_regs(in, fm, f2, tau, d, k);
+        k[13] = 0.f;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) Kp[i] = pack2(k[2 * i], k[2 * i + 1]);
+    };
+    auto unpack_tmp = [&](const unsigned long long *T2) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) unpack2(T2[i], tmp[2 * i], tmp[2 * i + 1]);
+    };
+    unsigned long long Tm[NP];
+    stage(x);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        A[i] = Kp[i];
+        Tm[i] = fma2(H2, Kp[i], X[i]);
     }
-    quad_deriv_regs(tmp, fm, f2, tau, d, k);
+    unpack_tmp(Tm);
+    stage(tmp);
 #pragma unroll
-    for (int i = 0; i < 13; ++i) {
-        acc[i] += 2.0f * k[i];
-        tmp[i] = x[i] + h * k[i];
+    for (int i = 0; i < NP; ++i) {
+        A[i] = fma2(TWO2, Kp[i], A[i]);
+        Tm[i] = fma2(H2, Kp[i], X[i]);
     }
-    quad_deriv_regs(tmp, fm, f2, tau, d, k);
+    unpack_tmp(Tm);
+    stage(tmp);
 #pragma unroll
-    for (int i = 0; i < 13; ++i) {
-        acc[i] += 2.0f * k[i];
-        tmp[i] = x[i] + dt * k[i];
+    for (int i = 0; i < NP; ++i) {
+        A[i] = fma2(TWO2, Kp[i], A[i]);
+        Tm[i] = fma2(DT2, Kp[i], X[i]);
     }
-    quad_deriv_regs(tmp, fm, f2, tau, d, k);
-    const float d6 = dt / 6.0f;
+    unpack_tmp(Tm);
+    stage(tmp);
 #pragma unroll
-    for (int i = 0; i < 13; ++i) x[i] += d6 * (acc[i] + k[i]);
+    for (int i = 0; i < NP; ++i) X[i] = fma2(D62, add2(A[i], Kp[i]), X[i]);
+    float pad;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) unpack2(X[i], x[2 * i], i < NP - 1 ? x[2 * i + 1] : pad);
     const float inv = rsqrtf((x[6] * x[6] + x[7] * x[7]) + (x[8] * x[8] + x[9] * x[9]));
 #pragma unroll
     for (int i = 6; i < 10; ++i) x[i] *= inv;
