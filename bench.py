@@ -90,9 +90,11 @@ def job_throughput(rollout_steps_per_rank, world, ms_max):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms in the
+    background, each with nvidia-smi's own timestamp, so that only the samples
+    taken inside the timed region are summarised."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -106,7 +108,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
@@ -118,7 +120,18 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
-    def stop(self):
+    @staticmethod
+    def _epoch(stamp):
+        """nvidia-smi's local-time stamp ("2026/12/03 18:40:01.123") as epoch seconds."""
+        try:
+            day, frac = stamp.rsplit(".", 1)
+            return time.mktime(time.strptime(day, "%Y/%m/%d %H:%M:%S")) + float("0." + frac)
+        except (ValueError, OverflowError):
+            return None
+
+    def stop(self, region=None):
+        """Summary of the samples inside region = (t0, t1) (epoch seconds,
+        widened by one sampling period); of every sample if none fell inside."""
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -128,24 +141,36 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        return self.summarise(self.lines, region)
+
+    @classmethod
+    def summarise(cls, lines, region=None):
+        rows = []
+        for ln in lines:
             parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                rows.append((cls._epoch(parts[0]), float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-            for name, flag in zip(names, parts[5:9]):
+        if not rows:
+            return None
+        inside = rows
+        if region is not None:
+            t0, t1 = region[0] - 0.02, region[1] + 0.02
+            sel = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
+            if sel:
+                inside = sel
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in inside:
+            for name, flag in zip(names, r[3]):
                 if flag.lower() == "active":
                     reasons.add(name)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(r[1] for r in inside),
+                "sm_max_mhz": max(r[2] for r in inside), "reasons": sorted(reasons),
+                "samples": len(inside), "in_timed_region": inside is not rows or region is None}
 
 
 def measured_peaks():
@@ -344,7 +369,7 @@ def workload_config(p):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -393,6 +418,7 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     t_region = time.perf_counter()
+    wall0 = time.time()
     for i in range(args.steps):
         flush.fill_(float(i))
         starts[i].record(stream)
@@ -400,6 +426,7 @@ def main():
         ends[i].record(stream)
     torch.cuda.synchronize()
     region_s = time.perf_counter() - t_region
+    wall1 = time.time()
     if world > 1:
         torch.distributed.barrier()
     # Per-kernel durations: a second pass of the same timed loop with the
@@ -413,7 +440,7 @@ def main():
     torch.cuda.synchronize()
     ctl.profile(False)
     prof = ctl.profile_read()
-    clk = clocks.stop()
+    clk = clocks.stop((wall0, wall1))
     per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = max_over_ranks(sum(per_step) / len(per_step), dev, world)
     rollout_steps = p["K"] * p["T"]

@@ -1,4 +1,4 @@
-"""Host-side logic of bench.py's multi-rank path, on CPU.
+"""Host-side logic of bench.py, on CPU: the multi-rank path and the clock summary.
 
 Multi-GPU runs are independent replicas (weak scaling): the only exchange is
 the maximum of the per-rank step times.  These tests run that exchange with
@@ -69,3 +69,23 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_clock_summary_keeps_the_timed_region():
+    import time
+    import bench
+    t0 = time.mktime(time.strptime("2026/12/03 18:40:01", "%Y/%m/%d %H:%M:%S"))
+    lines = [
+        "2026/12/03 18:40:00.500, 0, 1200, 2070, 300.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "2026/12/03 18:40:01.010, 0, 2070, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "2026/12/03 18:40:01.030, 0, 2055, 2070, 910.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "2026/12/03 18:40:02.000, 0, 1400, 2070, 300.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+    ]
+    d = bench.ClockSampler.summarise(lines, (t0, t0 + 0.05))
+    assert d["samples"] == 2 and d["in_timed_region"]
+    assert d["sm_mhz"] == (2070 + 2055) / 2 and d["sm_max_mhz"] == 2070
+    assert d["reasons"] == ["sw_power_cap"]
+    # nothing inside: every sample, flagged
+    d = bench.ClockSampler.summarise(lines, (t0 + 100, t0 + 101))
+    assert d["samples"] == 4 and not d["in_timed_region"]
