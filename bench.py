@@ -378,10 +378,14 @@ def main():
     ap.add_argument("--K", type=int, default=None, help="override the sample count")
     ap.add_argument("--workload", default="quadrotor", choices=sorted(FLOPS_PER_ROLLOUT_STEP),
                     help="quadrotor (configuration 1, the headline) or a diagnostic run")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
+                    help="bf16: the bicycle workload's MLP on the tensor cores (diagnostic)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     p = make_workload(args.workload, args.K)
+    if args.precision == "bf16" and args.workload != "bicycle":
+        ap.error("--precision bf16 applies to the bicycle workload")
     if args.impl == "reference":
         return reference_arm(args, p)
 
@@ -396,7 +400,8 @@ def main():
 
     import paper_2409_07563_gb300 as m
     m.build()
-    ctl = m.MPPI.from_problem(p)
+    ctl = m.MPPI.from_problem(
+        p, precision=m.MPPI_PREC_BF16_MLP if args.precision == "bf16" else m.MPPI_PREC_FP32)
     x0 = torch.tensor(p["x0"], dtype=torch.float32, device=dev)
     u_nom = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device=dev)
     u_new = torch.empty_like(u_nom)
@@ -471,13 +476,25 @@ def main():
     upd_ms, upd_n = prof["update"]
     roll_avg_ms = roll_ms / max(roll_n, 1)
     achieved = FLOPS_PER_ROLLOUT_STEP[args.workload] * rollout_steps / (roll_avg_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+    kernel_name = KERNEL_NAME[args.workload]
+    if args.precision == "bf16":
+        # the MLP flops on the BF16 tensor pipe against its measured peak
+        mlp = 2 * (6 * 64 + 64 * 64 + 64 * 4) * rollout_steps / (roll_avg_ms * 1e-3) / 1e12
+        bf16_peak = measured_peaks().get("bf16_tflops", 1979.2)
+        achieved, peak_tflops = mlp, bf16_peak
+        kernel_name = "bicycle_mlp_bf16_kernel (MLP on mma.sync BF16, FP32 accumulate)"
+    roofline = {"bound": "tensor" if args.precision == "bf16" else "alu",
+                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": KERNEL_NAME[args.workload],
+                "kernel": kernel_name,
                 "kernel_ms": roll_avg_ms, "update_kernel_ms": upd_ms / max(upd_n, 1),
-                "peak_note": (f"FP32 pipe: {props.multi_processor_count} SMs x 128 lanes x 2 "
+                "peak_note": ("measured BF16 GEMM burst (MEASURED_PEAKS.json), MLP flops only"
+                              if args.precision == "bf16" else
+                              f"FP32 pipe: {props.multi_processor_count} SMs x 128 lanes x 2 "
                               f"x {sm_max:.0f} MHz (max SM clock)")}
     traffic_file = os.path.join(ROOT, "profiles", f"rollout_{args.workload}_traffic.json")
+    if args.precision == "bf16":
+        traffic_file = os.path.join(ROOT, "profiles", "rollout_bicycle_bf16_traffic.json")
     if os.path.exists(traffic_file):
         try:
             with open(traffic_file) as f:
