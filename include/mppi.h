@@ -144,7 +144,9 @@ typedef struct {
     int precision;            /* mppi_precision (default FP32) */
     uint64_t seed;            /* Philox key (default 0) */
     int block_threads;        /* rollout block size (multiple of 32, <= 256; variant 3:
-                                 multiple of 64, <= 512; variant 4: 128 or 256);
+                                 multiple of 64, <= 512; variant 4: 128 or 256;
+                                 BF16_MLP: 64, 128, 192 or 256, a dynamics warp
+                                 and a noise-and-cost warp per 32 samples);
                                  0 = automatic */
     int rollout_variant;      /* 0 automatic, 1 one sample per thread, 2 four lanes per
                                  sample, 3 four lanes per sample with a dynamics warp

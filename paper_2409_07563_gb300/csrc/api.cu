@@ -116,12 +116,19 @@ void plan_launch(mppi_ctx &c) {
                  : split ? mppi::kVariantQuadSplit
                  : group ? mppi::kVariantQuadGroup
                          : mppi::kVariantGeneric;
-    const int lanes = split ? 8 : pair1 ? roles : group ? 4 : 1;  // threads per sample
+    const int lanes = mlp_tc ? 2 : split ? 8 : pair1 ? roles : group ? 4 : 1;  // threads per sample
     const long threads_needed = static_cast<long>(c.K) * lanes;
     if (c.block_threads > 0) {
         pl.rollout_threads = c.block_threads;
     } else if (mlp_tc) {
-        pl.rollout_threads = 64;                 // two warps of 32 samples
+        // warp pairs of 32 samples spread over every SM first, at most four
+        // per block: a block's warps occupy consecutive warp slots, so four
+        // pairs put one dynamics warp on each SM sub-partition (measured on
+        // GB300 at K = 16384, T = 100: 122 us per step against 166 for one
+        // pair per block, whose dynamics warps share two sub-partitions)
+        const long groups = (static_cast<long>(c.K) + 31) / 32;
+        const long per_sm = (groups + c.num_sms - 1) / c.num_sms;
+        pl.rollout_threads = 64 * static_cast<int>(std::min(4L, std::max(1L, per_sm)));
     } else if (pair1) {
         // warp groups of 32 samples spread over every SM first, at most two
         // groups per block (K = 8192: 256 groups, two per block on 128 SMs)
@@ -276,6 +283,7 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     if (o.rollout_variant < 0 || o.rollout_variant > 4) return MPPI_ERR_INVALID_ARG;
     if (o.rollout_variant == 3 && o.block_threads % 64 != 0) return MPPI_ERR_INVALID_ARG;
     if (o.rollout_variant == 4 && o.block_threads % 128 != 0) return MPPI_ERR_INVALID_ARG;
+    if (o.precision == MPPI_PREC_BF16_MLP && o.block_threads % 64 != 0) return MPPI_ERR_INVALID_ARG;
     if (o.rollout_variant >= 2 &&
         (dyn->kind != MPPI_DYN_QUADROTOR ||
          (cost->kind == MPPI_COST_QUAD_OBSTACLES && cost->n_params > 33 + 4 * 32)))

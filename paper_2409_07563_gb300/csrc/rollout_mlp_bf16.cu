@@ -1,20 +1,35 @@
 // rollout_mlp_bf16.cu -- bicycle + residual MLP rollout with the MLP on the
 // tensor cores (BF16 operands, FP32 accumulation), steps a1-a3 and a6.
 //
-// One warp carries 32 samples, one per lane, for the noise, the kinematic
-// bicycle (FP32, accurate sincosf/tanf), the costmap and speed cost and the
-// importance term.  Every step the 32 samples' MLP inputs [v, delta, e1, e2,
-// u_a, u_delta] go to a per-warp shared tile (BF16, 32 x 8) and the MLP
-// 6 -> 64 -> 64 -> 4 runs as two 16-row tiles of warp-level MMAs:
-//   layer 1  mma.m16n8k8   8 output tiles   (K = 6 padded to 8)
-//   layer 2  mma.m16n8k16  8 x 4 tiles
-//   layer 3  mma.m16n8k16  1 x 4 tiles      (N = 4 padded to 8)
-// Weights and biases live in registers as MMA fragments for the whole
-// rollout; a layer's FP32 accumulators, after tanh (tanh.approx, whose error
-// is below the BF16 rounding that follows) and BF16 rounding, are directly
-// the next layer's A fragments (the m16n8 accumulator layout of two adjacent
-// 8-column tiles equals the m16n8k16 A layout), so activations never leave
-// registers.  The 4 outputs per sample return through a per-warp FP32 tile.
+// Each group of 32 samples is served by a pair of warps, one sample per lane
+// in each:
+//   dynamics warp  every step the 32 samples' MLP inputs [v, delta, e1, e2,
+//                  u_a, u_delta] go to a per-warp shared tile (BF16, 32 x 8)
+//                  and the MLP 6 -> 64 -> 64 -> 4 runs as two 16-row tiles of
+//                  warp-level MMAs:
+//                    layer 1  mma.m16n8k8   8 output tiles   (K = 6 padded to 8)
+//                    layer 2  mma.m16n8k16  8 x 4 tiles
+//                    layer 3  mma.m16n8k16  1 x 4 tiles      (N = 4 padded to 8)
+//                  (both halves layer by layer, two independent chains),
+//                  then Euler on the MLP's inputs (v, delta, e1, e2)
+//   cost warp      the noise of both channels (Philox blocks of four steps,
+//                  Box-Muller), v_t = u_t + sigma z_t with the importance
+//                  term; the pose (x, y, yaw) of the kinematic bicycle (FP32,
+//                  accurate sincosf/tanf, Euler) from v and delta before the
+//                  step and the yaw-rate residual -- the pose feeds nothing
+//                  back into the MLP, so it leaves the dynamics warp's chain;
+//                  the costmap (bilinear) and speed cost of x_{t+1}
+// They exchange v_t and (v, delta, r_yaw, v') of each step through a double-buffered
+// shared ring of four steps per half and meet at one named barrier per half
+// (bar.sync with the pair's id, 64 threads); both execute the same number of
+// barriers (the loops depend on T only).
+// Weights and biases live in the dynamics warp's registers as MMA fragments
+// for the whole rollout; a layer's FP32 accumulators, after tanh (tanh.approx,
+// whose error is below the BF16 rounding that follows) and BF16 rounding, are
+// directly the next layer's A fragments (the m16n8 accumulator layout of two
+// adjacent 8-column tiles equals the m16n8k16 A layout), so activations never
+// leave registers.  The 4 outputs per sample return through a per-warp FP32
+// tile.
 #include <cuda_bf16.h>
 
 #include "device_common.cuh"
@@ -30,16 +45,19 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-__device__ __forceinline__ float tanh_approx(float x) {
-    float y;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+// tanh of two BF16 values at once (one MUFU operation for both lanes of the
+// pair): the pre-activations are rounded to BF16 first, then tanh, whose
+// BF16 result is directly an MMA operand half.
+__device__ __forceinline__ uint32_t tanh_bf16x2(uint32_t x) {
+    uint32_t y;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(x));
     return y;
 }
 
 // D = A (16x8, row) * B (8x8, col) + C, BF16 in, FP32 accumulate.
 __device__ __forceinline__ void mma_16x8x8(float d[4], uint32_t a0, uint32_t a1, uint32_t b0,
                                            const float c[4]) {
-    asm volatile(
+    asm(
         "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
         "{%7,%8,%9,%10};"
         : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
@@ -49,7 +67,7 @@ __device__ __forceinline__ void mma_16x8x8(float d[4], uint32_t a0, uint32_t a1,
 // D = A (16x16, row) * B (16x8, col) + C.
 __device__ __forceinline__ void mma_16x8x16(float d[4], const uint32_t a[4], uint32_t b0,
                                             uint32_t b1, const float c[4]) {
-    asm volatile(
+    asm(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
         "{%8,%9}, {%10,%11,%12,%13};"
         : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
@@ -85,155 +103,249 @@ struct WarpTiles {
     float R[32][8];     // FP32 outputs, 32 rows x 8 columns
 };
 
+constexpr int kMlpH = 4;                     // steps per ring half (one Philox block)
+constexpr int kMlpRing = 2 * kMlpH * kWarp;  // entries per ring: [half][step][lane]
+
+__device__ __forceinline__ void mlp_pair_sync(int id) {
+    asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
+// Block = G pairs: warps [0, G) run the MLP and the kinematics, [G, 2G) the
+// noise and the cost; pair j synchronises on named barrier 1 + j.
 __global__ void __launch_bounds__(256) bicycle_mlp_bf16_kernel(const StepParams p) {
     extern __shared__ __align__(16) float smem[];
     const int T = p.T;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int G = nt / (2 * kWarp);
+    const int lane = tid & 31, warp = tid >> 5;
+    const int role = warp / G, pair = warp % G;
     float *s_u = smem;                                   // 2T
     float *s_cost = s_u + round_up4(2 * T);              // 8
     float *s_red = s_cost + 8;                           // kRedFloats
-    WarpTiles *tiles = reinterpret_cast<WarpTiles *>(s_red + kRedFloats);
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5;
+    WarpTiles *tiles = reinterpret_cast<WarpTiles *>(s_red + kRedFloats);  // G
+    float2 *ring_v = reinterpret_cast<float2 *>(tiles + G) + pair * kMlpRing;
+    float4 *ring_x = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(tiles + G) + G * kMlpRing) +
+                     pair * kMlpRing;
     wait_for_predecessor();
     for (int i = tid; i < 2 * T; i += nt) s_u[i] = p.u_nom[i];
     CostmapSpeedCost::prepare(p.cost_params, s_cost, tid, nt);
     __syncthreads();
-    WarpTiles &tile = tiles[warp];
 
-    // ---- weight and bias fragments (registers for the whole rollout) ----
-    const MlpView mv = mlp_view(p.dyn_params);
-    const int g = lane >> 2, t4 = lane & 3;
-    uint32_t B1[8], B2[8][4][2], B3[4][2];
-    float C1[8][2], C2[8][2], C3[2];
-#pragma unroll
-    for (int n = 0; n < 8; ++n) {
-        const int row = 8 * n + g;
-        const float w0 = 2 * t4 < 6 ? mv.W1[row * 6 + 2 * t4] : 0.f;
-        const float w1 = 2 * t4 + 1 < 6 ? mv.W1[row * 6 + 2 * t4 + 1] : 0.f;
-        B1[n] = pack_bf16x2(w0, w1);
-        C1[n][0] = mv.b1[8 * n + 2 * t4];
-        C1[n][1] = mv.b1[8 * n + 2 * t4 + 1];
-        C2[n][0] = mv.b2[8 * n + 2 * t4];
-        C2[n][1] = mv.b2[8 * n + 2 * t4 + 1];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float *w = mv.W2 + row * 64 + 16 * k;
-            B2[n][k][0] = pack_bf16x2(w[2 * t4], w[2 * t4 + 1]);
-            B2[n][k][1] = pack_bf16x2(w[8 + 2 * t4], w[8 + 2 * t4 + 1]);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const bool real = g < 4;
-        const float *w = mv.W3 + (real ? g : 0) * 64 + 16 * k;
-        B3[k][0] = real ? pack_bf16x2(w[2 * t4], w[2 * t4 + 1]) : 0u;
-        B3[k][1] = real ? pack_bf16x2(w[8 + 2 * t4], w[8 + 2 * t4 + 1]) : 0u;
-    }
-    C3[0] = 2 * t4 < 4 ? mv.b3[2 * t4] : 0.f;
-    C3[1] = 2 * t4 + 1 < 4 ? mv.b3[2 * t4 + 1] : 0.f;
-    const float inv_L = 1.0f / p.dyn_params[0];
-
-    // ---- one sample per lane ----
-    const int k = blockIdx.x * nt + tid;
-    const bool active = k < p.K;
-    float x[7];
-#pragma unroll
-    for (int i = 0; i < 7; ++i) x[i] = p.x0[i];
-    const NoiseKey nk = make_noise_key(p.seed, *p.counter);
-    const CostCtx cc{p.map, p.map_h, p.map_w};
-    const float sig0 = p.sigma[0], sig1 = p.sigma[1], iv0 = p.ivar[0], iv1 = p.ivar[1];
-    const int QT = (T + 3) / 4;
-    CompSum J;
-    float z0[4], z1[4];
-    for (int t = 0; t < T; ++t) {
-        const int s = t & 3;
-        if (s == 0) {
-            box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(t / 4)), z0);
-            box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(QT + t / 4)), z1);
-        }
-        const float za = s == 0 ? z0[0] : s == 1 ? z0[1] : s == 2 ? z0[2] : z0[3];
-        const float zd = s == 0 ? z1[0] : s == 1 ? z1[1] : s == 2 ? z1[2] : z1[3];
-        const float ua = s_u[2 * t], ud = s_u[2 * t + 1];
-        const float va = ua + sig0 * za, vd = ud + sig1 * zd;
-        const float is = (va - 0.5f * ua) * (ua * iv0) + (vd - 0.5f * ud) * (ud * iv1);
-
-        // MLP inputs of this lane's sample -> shared tile row
-        __syncwarp();
-        tile.X[lane][0] = pack_bf16x2(x[3], x[4]);
-        tile.X[lane][1] = pack_bf16x2(x[5], x[6]);
-        tile.X[lane][2] = pack_bf16x2(va, vd);
-        tile.X[lane][3] = 0u;
-        __syncwarp();
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            // layer 1: A = rows 16 half .. + 15, K = 8
-            uint32_t a0, a1;
-            ldmatrix_x2(a0, a1, &tile.X[16 * half + (lane & 15)][0]);
-            uint32_t A2[4][4];
-#pragma unroll
-            for (int n = 0; n < 8; ++n) {
-                float c[4] = {C1[n][0], C1[n][1], C1[n][0], C1[n][1]};
-                float d[4];
-                mma_16x8x8(d, a0, a1, B1[n], c);
-                const uint32_t lo = pack_bf16x2(tanh_approx(d[0]), tanh_approx(d[1]));
-                const uint32_t hi = pack_bf16x2(tanh_approx(d[2]), tanh_approx(d[3]));
-                // n-tiles 2k, 2k+1 form k-tile k of the next layer
-                A2[n >> 1][(n & 1) ? 2 : 0] = lo;
-                A2[n >> 1][(n & 1) ? 3 : 1] = hi;
-            }
-            // layer 2: 64 -> 64
-            uint32_t A3[4][4];
-#pragma unroll
-            for (int n = 0; n < 8; ++n) {
-                float acc[4] = {C2[n][0], C2[n][1], C2[n][0], C2[n][1]};
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) mma_16x8x16(acc, A2[kk], B2[n][kk][0], B2[n][kk][1], acc);
-                const uint32_t lo = pack_bf16x2(tanh_approx(acc[0]), tanh_approx(acc[1]));
-                const uint32_t hi = pack_bf16x2(tanh_approx(acc[2]), tanh_approx(acc[3]));
-                A3[n >> 1][(n & 1) ? 2 : 0] = lo;
-                A3[n >> 1][(n & 1) ? 3 : 1] = hi;
-            }
-            // layer 3: 64 -> 4 (8 with zero padding)
-            float out[4] = {C3[0], C3[1], C3[0], C3[1]};
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) mma_16x8x16(out, A3[kk], B3[kk][0], B3[kk][1], out);
-            *reinterpret_cast<float2 *>(&tile.R[16 * half + g][2 * t4]) = make_float2(out[0], out[1]);
-            *reinterpret_cast<float2 *>(&tile.R[16 * half + g + 8][2 * t4]) =
-                make_float2(out[2], out[3]);
-        }
-        __syncwarp();
-        const float4 r = *reinterpret_cast<const float4 *>(&tile.R[lane][0]);
-
-        // kinematic bicycle + residual, Euler
-        float sn, cs;
-        sincosf(x[2], &sn, &cs);
-        const float xd0 = x[3] * cs, xd1 = x[3] * sn;
-        const float xd2 = x[3] * tanf(x[4]) * inv_L + r.x;
-        const float xd3 = va + r.y;
-        x[0] += p.dt * xd0;
-        x[1] += p.dt * xd1;
-        x[2] += p.dt * xd2;
-        x[3] += p.dt * xd3;
-        x[4] += p.dt * vd;
-        x[5] += p.dt * r.z;
-        x[6] += p.dt * r.w;
-        const float v2[2] = {va, vd};
-        J.add(CostmapSpeedCost::running(x, v2, s_cost, cc) + p.lam_beta * is);
-    }
-    J.add(CostmapSpeedCost::terminal(x, s_cost, cc));
+    const int k = (blockIdx.x * G + pair) * kWarp + lane;
+    const int nh = (T + kMlpH - 1) / kMlpH;
+    const int bar_id = 1 + pair;
     float S = __int_as_float(0x7f800000);
-    if (active) {
-        S = J.value();
-        p.S[k] = S;
+    int k_out = -1;
+    if (role == 0) {
+        WarpTiles &tile = tiles[pair];
+        // ---- weight and bias fragments (registers for the whole rollout) ----
+        const MlpView mv = mlp_view(p.dyn_params);
+        const int g = lane >> 2, t4 = lane & 3;
+        uint32_t B1[8], B2[8][4][2], B3[4][2];
+        float C1[8][2], C2[8][2], C3[2];
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            const int row = 8 * n + g;
+            const float w0 = 2 * t4 < 6 ? mv.W1[row * 6 + 2 * t4] : 0.f;
+            const float w1 = 2 * t4 + 1 < 6 ? mv.W1[row * 6 + 2 * t4 + 1] : 0.f;
+            B1[n] = pack_bf16x2(w0, w1);
+            C1[n][0] = mv.b1[8 * n + 2 * t4];
+            C1[n][1] = mv.b1[8 * n + 2 * t4 + 1];
+            C2[n][0] = mv.b2[8 * n + 2 * t4];
+            C2[n][1] = mv.b2[8 * n + 2 * t4 + 1];
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const float *w = mv.W2 + row * 64 + 16 * kk;
+                B2[n][kk][0] = pack_bf16x2(w[2 * t4], w[2 * t4 + 1]);
+                B2[n][kk][1] = pack_bf16x2(w[8 + 2 * t4], w[8 + 2 * t4 + 1]);
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const bool real = g < 4;
+            const float *w = mv.W3 + (real ? g : 0) * 64 + 16 * kk;
+            B3[kk][0] = real ? pack_bf16x2(w[2 * t4], w[2 * t4 + 1]) : 0u;
+            B3[kk][1] = real ? pack_bf16x2(w[8 + 2 * t4], w[8 + 2 * t4 + 1]) : 0u;
+        }
+        C3[0] = 2 * t4 < 4 ? mv.b3[2 * t4] : 0.f;
+        C3[1] = 2 * t4 + 1 < 4 ? mv.b3[2 * t4 + 1] : 0.f;
+        // the MLP inputs (v, delta, e1, e2) evolve here; the pose (x, y, yaw),
+        // which feeds nothing back, is integrated by the cost warp
+        float x3 = p.x0[3], x4 = p.x0[4], x5 = p.x0[5], x6 = p.x0[6];
+        mlp_pair_sync(bar_id);  // controls of half 0 are in the ring
+        for (int hh = 0; hh < nh; ++hh) {
+            const float2 *vb = ring_v + (hh & 1) * kMlpH * kWarp;
+            float4 *xb = ring_x + (hh & 1) * kMlpH * kWarp;
+            const int ns = min(kMlpH, T - hh * kMlpH);
+#pragma unroll 1
+            for (int s = 0; s < ns; ++s) {
+                const float2 v2 = vb[s * kWarp + lane];
+                const float va = v2.x, vd = v2.y;
+                // MLP inputs of this lane's sample -> shared tile row
+                __syncwarp();
+                tile.X[lane][0] = pack_bf16x2(x3, x4);
+                tile.X[lane][1] = pack_bf16x2(x5, x6);
+                tile.X[lane][2] = pack_bf16x2(va, vd);
+                tile.X[lane][3] = 0u;
+                __syncwarp();
+                // both 16-row halves layer by layer (independent chains)
+                uint32_t a1[2][2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) ldmatrix_x2(a1[h][0], a1[h][1], &tile.X[16 * h + (lane & 15)][0]);
+                // layer 1: 6 (padded to 8) -> 64
+                uint32_t A2[2][4][4];
+#pragma unroll
+                for (int n = 0; n < 8; ++n) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float c[4] = {C1[n][0], C1[n][1], C1[n][0], C1[n][1]};
+                        float d[4];
+                        mma_16x8x8(d, a1[h][0], a1[h][1], B1[n], c);
+                        // n-tiles 2k, 2k+1 form k-tile k of the next layer
+                        A2[h][n >> 1][(n & 1) ? 2 : 0] = tanh_bf16x2(pack_bf16x2(d[0], d[1]));
+                        A2[h][n >> 1][(n & 1) ? 3 : 1] = tanh_bf16x2(pack_bf16x2(d[2], d[3]));
+                    }
+                }
+                // layer 2: 64 -> 64
+                uint32_t A3[2][4][4];
+#pragma unroll
+                for (int n = 0; n < 8; ++n) {
+                    float acc[2][4];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        acc[h][0] = acc[h][2] = C2[n][0];
+                        acc[h][1] = acc[h][3] = C2[n][1];
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+                            mma_16x8x16(acc[h], A2[h][kk], B2[n][kk][0], B2[n][kk][1], acc[h]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        A3[h][n >> 1][(n & 1) ? 2 : 0] = tanh_bf16x2(pack_bf16x2(acc[h][0], acc[h][1]));
+                        A3[h][n >> 1][(n & 1) ? 3 : 1] = tanh_bf16x2(pack_bf16x2(acc[h][2], acc[h][3]));
+                    }
+                }
+                // layer 3: 64 -> 4 (8 with zero padding)
+                float out[2][4];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    out[h][0] = out[h][2] = C3[0];
+                    out[h][1] = out[h][3] = C3[1];
+                }
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) mma_16x8x16(out[h], A3[h][kk], B3[kk][0], B3[kk][1], out[h]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    *reinterpret_cast<float2 *>(&tile.R[16 * h + g][2 * t4]) = make_float2(out[h][0], out[h][1]);
+                    *reinterpret_cast<float2 *>(&tile.R[16 * h + g + 8][2 * t4]) =
+                        make_float2(out[h][2], out[h][3]);
+                }
+                __syncwarp();
+                const float4 r = *reinterpret_cast<const float4 *>(&tile.R[lane][0]);
+                // Euler on (v, delta, e1, e2); the cost warp takes v and delta
+                // before the step and the yaw-rate residual for the pose
+                const float v_old = x3, d_old = x4;
+                x3 += p.dt * (va + r.y);
+                x4 += p.dt * vd;
+                x5 += p.dt * r.z;
+                x6 += p.dt * r.w;
+                xb[s * kWarp + lane] = make_float4(v_old, d_old, r.x, x3);
+            }
+            mlp_pair_sync(bar_id);
+        }
+    } else {
+        const NoiseKey nk = make_noise_key(p.seed, *p.counter);
+        const CostCtx cc{p.map, p.map_h, p.map_w};
+        const float sig0 = p.sigma[0], sig1 = p.sigma[1], iv0 = p.ivar[0], iv1 = p.ivar[1];
+        const int QT = (T + 3) / 4;
+        CompSum J;
+        // v_t of half hc with the importance term
+        auto controls = [&](int hc) {
+            float2 *vb = ring_v + (hc & 1) * kMlpH * kWarp;
+            const int nc = min(kMlpH, T - hc * kMlpH);
+            float z0[4], z1[4];
+            box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(hc)), z0);
+            box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(QT + hc)), z1);
+#pragma unroll
+            for (int s = 0; s < kMlpH; ++s) {
+                if (s < nc) {
+                    const int t = hc * kMlpH + s;
+                    const float ua = s_u[2 * t], ud = s_u[2 * t + 1];
+                    const float va = ua + sig0 * z0[s], vd = ud + sig1 * z1[s];
+                    vb[s * kWarp + lane] = make_float2(va, vd);
+                    J.add(p.lam_beta *
+                          ((va - 0.5f * ua) * (ua * iv0) + (vd - 0.5f * ud) * (ud * iv1)));
+                }
+            }
+        };
+        const float inv_L = 1.0f / p.dyn_params[0];
+        float px = p.x0[0], py = p.x0[1], yaw = p.x0[2];
+        // pose of x_{t+1} (kinematic bicycle, Euler) from v, delta before the
+        // step and the yaw-rate residual; running cost of x_{t+1}; the
+        // terminal cost on x_T
+        // In phases over the half's four steps so that independent work
+        // overlaps: the four tangents, the serial pose chain, the four
+        // costmap lookups, then the sums in step order.  Steps past T occur
+        // only in the last half; their poses are computed from stale ring
+        // entries (every lookup index is clamped into the map) and never
+        // scored.
+        auto states = [&](int hs) {
+            const float4 *xb = ring_x + (hs & 1) * kMlpH * kWarp;
+            const int nx = min(kMlpH, T - hs * kMlpH);
+            float4 q[kMlpH];
+            float tn[kMlpH], cx[kMlpH], cy[kMlpH], cst[kMlpH];
+#pragma unroll
+            for (int s = 0; s < kMlpH; ++s) q[s] = xb[s * kWarp + lane];  // v, delta, r_yaw, v'
+#pragma unroll
+            for (int s = 0; s < kMlpH; ++s) tn[s] = tanf(q[s].y);
+#pragma unroll
+            for (int s = 0; s < kMlpH; ++s) {
+                float sn, cs;
+                sincosf(yaw, &sn, &cs);
+                const float xd0 = q[s].x * cs, xd1 = q[s].x * sn;
+                const float xd2 = q[s].x * tn[s] * inv_L + q[s].z;
+                px += p.dt * xd0;
+                py += p.dt * xd1;
+                yaw += p.dt * xd2;
+                cx[s] = px;
+                cy[s] = py;
+            }
+#pragma unroll
+            for (int s = 0; s < kMlpH; ++s) {
+                const float y[4] = {cx[s], cy[s], 0.f, q[s].w};  // x, y, (yaw unused), v
+                cst[s] = CostmapSpeedCost::state_cost(y, s_cost, cc);
+            }
+#pragma unroll
+            for (int s = 0; s < kMlpH; ++s)
+                if (s < nx) J.add(hs * kMlpH + s == T - 1 ? cst[s] + cst[s] : cst[s]);
+        };
+        controls(0);
+        mlp_pair_sync(bar_id);
+        for (int hh = 0; hh < nh; ++hh) {
+            if (hh + 1 < nh) controls(hh + 1);
+            if (hh >= 1) states(hh - 1);
+            mlp_pair_sync(bar_id);
+        }
+        states(nh - 1);
+        if (k < p.K) {
+            S = J.value();
+            k_out = k;
+            p.S[k] = S;
+        }
     }
-    block_weight_tail(p, S, active ? k : -1, s_red, blockDim.x, s_u);
+    block_weight_tail(p, S, k_out, s_red, kWarp * G, s_u);
 }
 
 }  // namespace
 
 size_t mlp_bf16_smem_bytes(const mppi_ctx &c, int threads) {
+    const size_t pairs = static_cast<size_t>(threads / (2 * kWarp));
     return sizeof(float) * static_cast<size_t>(round_up4(2 * c.T) + 8 + kRedFloats) +
-           sizeof(WarpTiles) * static_cast<size_t>(threads / 32);
+           pairs * (sizeof(WarpTiles) + kMlpRing * (sizeof(float2) + sizeof(float4)));
 }
 
 cudaError_t mlp_bf16_prepare(const mppi_ctx &c) {

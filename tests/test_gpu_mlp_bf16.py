@@ -67,3 +67,35 @@ def test_bf16_and_fp32_paths_agree_on_costs(m):
     g32 = run(m, p, m.MPPI_PREC_FP32)
     rel = np.abs(g16["costs"] - g32["costs"]) / np.maximum(1.0, np.abs(g32["costs"]))
     assert np.median(rel) <= 1e-3
+
+
+def run_opts(m, p, precision, **kw):
+    ctl = m.MPPI.from_problem(p, precision=precision, **kw)
+    x0 = torch.tensor(p["x0"], dtype=torch.float32, device="cuda")
+    u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device="cuda")
+    out = ctl.step(x0, u, want_weights=True, want_costs=True)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy().astype(np.float64) for k, v in out.items()}
+
+
+@pytest.mark.parametrize("bt", [64, 128, 192, 256])
+@pytest.mark.parametrize("K,T", [(2001, 9), (97, 1), (300, 4), (33, 5)])
+def test_bf16_mlp_warp_pairs_block_sizes(m, bt, K, T):
+    """Warp pairs (a dynamics warp and a noise-and-cost warp per 32 samples)
+    at every block size, with ragged K (samples beyond K computed and
+    discarded) and horizons that end inside a ring half or on its edge."""
+    p = as_f32_problem(W.bicycle_mlp(K=K, T=T, lam=100.0))
+    g = run_opts(m, p, m.MPPI_PREC_BF16_MLP, block_threads=bt)
+    o = oracle.mppi_step(p, n_threads=n_threads(), want_eps=True)
+    rel = np.abs(g["costs"] - o["S"]) / np.maximum(1.0, np.abs(o["S"]))
+    assert np.median(rel) <= 1e-3
+    assert rel.max() <= 2e-2
+    w_ref, st_ref, _ = oracle.weights(g["costs"], 100.0)
+    u_iso = p["u_nom"] + np.einsum("k,ktj->tj", w_ref, o["eps"])
+    assert np.all(np.abs(g["u_new"] - u_iso) <= 1e-5 * p["sigma"][None, :])
+
+
+def test_bf16_mlp_rejects_odd_warp_count(m):
+    p = as_f32_problem(W.bicycle_mlp(K=256, T=8, lam=1.0))
+    with pytest.raises(Exception):
+        m.MPPI.from_problem(p, precision=m.MPPI_PREC_BF16_MLP, block_threads=96)
