@@ -58,7 +58,7 @@ KERNEL_NAME = {
     "quadrotor": "quad_pair_kernel<true,false> (one sample per thread; dynamics, two noise and "
                  "a cost warp per 32 samples)",
     "cartpole": "rollout_kernel<CartpoleDyn, QuadraticCost<4,1>>",
-    "bicycle": "rollout_kernel<BicycleMlpDyn, CostmapSpeedCost>",
+    "bicycle": "bicycle_mlp_f32_kernel (four lanes per sample, FP32 CUDA cores)",
 }
 # FP32 pipe: 128 FP32 lanes per SM, 2 flops per FMA.
 FP32_LANES_PER_SM = 128
@@ -352,11 +352,17 @@ def extensions(m, dev, peak_tflops, bf16_peak):
         res[name] = time_steps_flushed(lambda: c.step_into(x0, u, un), 10, flush)
         c.close()
     mlp_tflops = 2 * (6 * 64 + 64 * 64 + 64 * 4) * p["K"] * p["T"] / (res["bf16"] * 1e-3) / 1e12
+    # the 128 hidden-layer tanh per rollout-step run on the XU (MUFU) pipe:
+    # 16 per clock per SM
+    props = torch.cuda.get_device_properties(dev)
+    xu_peak = props.multi_processor_count * 16 * measured_peaks().get("sm_max_mhz", 2070.0) * 1e6
+    tanh_rate = 128 * p["K"] * p["T"] / (res["bf16"] * 1e-3)
     out["bf16_mlp"] = {"workload": "bicycle + MLP 6-64-64-4, K=16384 T=100, costmap 512x512",
                        "ms_per_step": res["bf16"], "fp32_ms_per_step": res["fp32"],
                        "rollout_steps_per_s": p["K"] * p["T"] / (res["bf16"] * 1e-3),
                        "mlp_tflops": mlp_tflops,
-                       "bf16_tensor_frac": mlp_tflops / bf16_peak if bf16_peak else None}
+                       "bf16_tensor_frac": mlp_tflops / bf16_peak if bf16_peak else None,
+                       "tanh_per_s": tanh_rate, "xu_tanh_frac": tanh_rate / xu_peak}
     return out
 
 

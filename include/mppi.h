@@ -153,7 +153,10 @@ typedef struct {
                                  and a cost warp per eight samples, 4 one sample per
                                  thread with a dynamics warp, two noise warps and a
                                  cost warp per 32 samples (2-4: QUADROTOR with at most
-                                 32 obstacles) */
+                                 32 obstacles).  BICYCLE_MLP with COSTMAP_SPEED at
+                                 FP32: 0 takes four lanes per sample (the MLP's
+                                 hidden units split over the lanes), 1 one sample
+                                 per thread */
     int reserved[6];
 } mppi_options;
 

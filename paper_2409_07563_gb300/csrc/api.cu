@@ -111,12 +111,14 @@ void plan_launch(mppi_ctx &c) {
                        c.block_threads % 64 == 0;
     const bool group = quad && !pair1 && !split;
     const bool mlp_tc = c.precision == MPPI_PREC_BF16_MLP;
+    const bool mlp32 = mppi::mlp_f32_applicable(c) && c.variant_opt != mppi::kVariantGeneric;
     pl.variant = mlp_tc  ? mppi::kVariantMlpBf16
+                 : mlp32 ? mppi::kVariantMlpF32
                  : pair1 ? mppi::kVariantQuadPair
                  : split ? mppi::kVariantQuadSplit
                  : group ? mppi::kVariantQuadGroup
                          : mppi::kVariantGeneric;
-    const int lanes = mlp_tc ? 2 : split ? 8 : pair1 ? roles : group ? 4 : 1;  // threads per sample
+    const int lanes = mlp_tc ? 2 : mlp32 ? 4 : split ? 8 : pair1 ? roles : group ? 4 : 1;  // threads per sample
     const long threads_needed = static_cast<long>(c.K) * lanes;
     if (c.block_threads > 0) {
         pl.rollout_threads = c.block_threads;
@@ -129,6 +131,11 @@ void plan_launch(mppi_ctx &c) {
         const long groups = (static_cast<long>(c.K) + 31) / 32;
         const long per_sm = (groups + c.num_sms - 1) / c.num_sms;
         pl.rollout_threads = 64 * static_cast<int>(std::min(4L, std::max(1L, per_sm)));
+    } else if (mlp32) {
+        // eight samples per warp; two warps per block once there are two
+        // warps per SM (K = 16384: 1024 blocks, about seven per SM)
+        const long warps = (static_cast<long>(c.K) + 7) / 8;
+        pl.rollout_threads = warps >= 2L * c.num_sms ? 64 : 32;
     } else if (pair1) {
         // warp groups of 32 samples spread over every SM first, at most two
         // groups per block (K = 8192: 256 groups, two per block on 128 SMs)
@@ -382,6 +389,7 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
         : c->plan.variant == mppi::kVariantQuadSplit ? mppi::quad_split_smem_bytes(*c, c->plan.rollout_threads)
         : c->plan.variant == mppi::kVariantQuadPair ? mppi::quad_pair_smem_bytes(*c, c->plan.rollout_threads)
         : c->plan.variant == mppi::kVariantMlpBf16 ? mppi::mlp_bf16_smem_bytes(*c, c->plan.rollout_threads)
+        : c->plan.variant == mppi::kVariantMlpF32 ? mppi::mlp_f32_smem_bytes(*c, c->plan.rollout_threads)
                                                    : mppi::rollout_smem_bytes(*c);
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
@@ -393,7 +401,8 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
         (c->plan.variant == mppi::kVariantQuadGroup && (e = mppi::quad_group_prepare(*c)) != cudaSuccess) ||
         (c->plan.variant == mppi::kVariantQuadSplit && (e = mppi::quad_split_prepare(*c)) != cudaSuccess) ||
         (c->plan.variant == mppi::kVariantQuadPair && (e = mppi::quad_pair_prepare(*c)) != cudaSuccess) ||
-        (c->plan.variant == mppi::kVariantMlpBf16 && (e = mppi::mlp_bf16_prepare(*c)) != cudaSuccess)) {
+        (c->plan.variant == mppi::kVariantMlpBf16 && (e = mppi::mlp_bf16_prepare(*c)) != cudaSuccess) ||
+        (c->plan.variant == mppi::kVariantMlpF32 && (e = mppi::mlp_f32_prepare(*c)) != cudaSuccess)) {
         free_ctx(c);
         return MPPI_ERR_CUDA;
     }
@@ -432,6 +441,7 @@ mppi_status mppi_step(mppi_ctx *ctx, const float *x0_d, const float *u_nom_d, fl
             : ctx->plan.variant == mppi::kVariantQuadSplit ? mppi::launch_quad_split(*ctx, p)
             : ctx->plan.variant == mppi::kVariantQuadPair ? mppi::launch_quad_pair(*ctx, p)
             : ctx->plan.variant == mppi::kVariantMlpBf16 ? mppi::launch_mlp_bf16(*ctx, p)
+            : ctx->plan.variant == mppi::kVariantMlpF32 ? mppi::launch_mlp_f32(*ctx, p)
                                                          : mppi::launch_rollout(*ctx, p);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rollout launch");

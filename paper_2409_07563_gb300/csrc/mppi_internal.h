@@ -68,7 +68,8 @@ enum RolloutVariant {
     kVariantQuadGroup = 2,
     kVariantQuadSplit = 3,
     kVariantQuadPair = 4,
-    kVariantMlpBf16 = 5
+    kVariantMlpBf16 = 5,
+    kVariantMlpF32 = 6
 };
 
 struct LaunchPlan {
@@ -141,7 +142,7 @@ cudaError_t quad_split_prepare(const mppi_ctx &c);
 cudaError_t launch_quad_split(const mppi_ctx &c, const StepParams &p);
 // rollout_quad_pair.cu: one sample per thread, dynamics / cost / crash warps per 32 samples
 bool quad_pair_applicable(const mppi_ctx &c);
-int quad_pair_roles(const mppi_ctx &c);  // warps per 32 samples: 3 with obstacles, else 2
+int quad_pair_roles(const mppi_ctx &c);  // warps per 32 samples (4)
 size_t quad_pair_smem_bytes(const mppi_ctx &c, int threads);
 cudaError_t quad_pair_prepare(const mppi_ctx &c);
 cudaError_t launch_quad_pair(const mppi_ctx &c, const StepParams &p);
@@ -149,5 +150,10 @@ cudaError_t launch_quad_pair(const mppi_ctx &c, const StepParams &p);
 size_t mlp_bf16_smem_bytes(const mppi_ctx &c, int threads);
 cudaError_t mlp_bf16_prepare(const mppi_ctx &c);
 cudaError_t launch_mlp_bf16(const mppi_ctx &c, const StepParams &p);
+// rollout_mlp_f32.cu: bicycle + MLP in FP32, four lanes per sample
+bool mlp_f32_applicable(const mppi_ctx &c);
+size_t mlp_f32_smem_bytes(const mppi_ctx &c, int threads);
+cudaError_t mlp_f32_prepare(const mppi_ctx &c);
+cudaError_t launch_mlp_f32(const mppi_ctx &c, const StepParams &p);
 
 }  // namespace mppi

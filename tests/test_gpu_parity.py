@@ -204,9 +204,21 @@ def test_quadrotor_lane_groups_quadratic_cost_only(m):
         compare(p, g)
 
 
-def test_bicycle_mlp_fp32_config_full(m):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_bicycle_mlp_fp32_config_full(m, variant):
+    """Automatic (four lanes per sample) and one sample per thread."""
     p = as_f32_problem(W.bicycle_mlp())
-    g, _ = run_gpu(m, p)
+    g, _ = run_gpu(m, p, rollout_variant=variant)
+    compare(p, g)
+
+
+@pytest.mark.parametrize("bt", [32, 64, 96, 128, 256])
+@pytest.mark.parametrize("K,T", [(2001, 21), (7, 9), (70, 1)])
+def test_bicycle_four_lanes_block_sizes(m, bt, K, T):
+    """FP32 MLP with four lanes per sample at every block size, ragged K (a
+    partial warp of samples) and horizons off the four-step noise blocks."""
+    p = as_f32_problem(W.bicycle_mlp(K=K, T=T, lam=5.0))
+    g, _ = run_gpu(m, p, block_threads=bt)
     compare(p, g)
 
 
@@ -228,9 +240,10 @@ def test_quadrotor_ragged(m, K, T, variant):
     compare(p, g)
 
 
-def test_bicycle_ragged(m):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_bicycle_ragged(m, variant):
     p = as_f32_problem(W.bicycle_mlp(K=2001, T=21, lam=5.0))
-    g, _ = run_gpu(m, p)
+    g, _ = run_gpu(m, p, rollout_variant=variant)
     compare(p, g)
 
 
