@@ -118,7 +118,8 @@ void plan_launch(mppi_ctx &c) {
                  : split ? mppi::kVariantQuadSplit
                  : group ? mppi::kVariantQuadGroup
                          : mppi::kVariantGeneric;
-    const int lanes = mlp_tc ? 2 : mlp32 ? 4 : split ? 8 : pair1 ? roles : group ? 4 : 1;  // threads per sample
+    // threads per sample (the FP32 MLP: four lanes per two samples)
+    const int lanes = mlp_tc ? 2 : mlp32 ? 2 : split ? 8 : pair1 ? roles : group ? 4 : 1;
     const long threads_needed = static_cast<long>(c.K) * lanes;
     if (c.block_threads > 0) {
         pl.rollout_threads = c.block_threads;
@@ -132,9 +133,9 @@ void plan_launch(mppi_ctx &c) {
         const long per_sm = (groups + c.num_sms - 1) / c.num_sms;
         pl.rollout_threads = 64 * static_cast<int>(std::min(4L, std::max(1L, per_sm)));
     } else if (mlp32) {
-        // eight samples per warp; two warps per block once there are two
-        // warps per SM (K = 16384: 1024 blocks, about seven per SM)
-        const long warps = (static_cast<long>(c.K) + 7) / 8;
+        // sixteen samples per warp; two warps per block once there are two
+        // warps per SM (K = 16384: 512 blocks, about seven warps per SM)
+        const long warps = (static_cast<long>(c.K) + 15) / 16;
         pl.rollout_threads = warps >= 2L * c.num_sms ? 64 : 32;
     } else if (pair1) {
         // warp groups of 32 samples spread over every SM first, at most two
