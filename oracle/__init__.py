@@ -82,6 +82,12 @@ def lib():
         L.oracle_weights.argtypes = [ctypes.c_int, _dp, ctypes.c_double, _dp, _dp]
         L.oracle_mppi_step.argtypes = [P, _dp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
         L.oracle_mppi_grad_cartpole.argtypes = [P, _dp, _dp, _dp, _dp, ctypes.c_int]
+        L.oracle_mppi_iterate.argtypes = [P, _dp, _dp, ctypes.c_int, ctypes.c_double, _dp, _dp,
+                                          _dp, _dp, ctypes.c_int]
+        L.oracle_nominal_trajectory.argtypes = [P, _dp, _dp, _dp]
+        L.oracle_nominal_trajectory.restype = None
+        L.oracle_shift.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp]
+        L.oracle_shift.restype = None
         L.oracle_max_threads.argtypes = []
     return _lib
 
@@ -220,6 +226,41 @@ def mppi_step(p, step=0, n_threads=1, x0=None, u_nom=None, want_eps=False):
     out = dict(u_new=u_new, w=w, S=S, stats=stats, status=st)
     if want_eps:
         out["eps"] = eps
+    return out
+
+
+def mppi_iterate(p, iterations, gamma, step=0, n_threads=1, x0=None, u_nom=None):
+    """Algorithm 1 with I iterations and the DMD-MPC step size gamma (Sec. V-B);
+    returns dict(u_new, w, S, stats, status) of the last iteration."""
+    P = Problem(p, step)
+    K, T, nu = p["K"], p["T"], p["nu"]
+    x0 = np.ascontiguousarray(p["x0"] if x0 is None else x0, float)
+    u = np.ascontiguousarray(p["u_nom"] if u_nom is None else u_nom, float)
+    u_new = np.zeros((T, nu))
+    w = np.zeros(K)
+    S = np.zeros(K)
+    stats = np.zeros(4)
+    st = lib().oracle_mppi_iterate(P.ref, _ptr(x0), _ptr(u), int(iterations), float(gamma),
+                                   _ptr(u_new), _ptr(w), _ptr(S), _ptr(stats), int(n_threads))
+    return dict(u_new=u_new, w=w, S=S, stats=stats, status=st)
+
+
+def nominal_trajectory(p, u, x0=None):
+    """States (T+1, nx) of x0 under the control sequence u (T, nu), no noise."""
+    P = Problem(p)
+    x0 = np.ascontiguousarray(p["x0"] if x0 is None else x0, float)
+    u = np.ascontiguousarray(u, float)
+    traj = np.zeros((p["T"] + 1, p["nx"]))
+    lib().oracle_nominal_trajectory(P.ref, _ptr(x0), _ptr(u), _ptr(traj))
+    return traj
+
+
+def shift(u, s):
+    """u shifted by s steps, the last s steps holding the final control."""
+    u = np.ascontiguousarray(u, float)
+    T, nu = u.shape
+    out = np.zeros_like(u)
+    lib().oracle_shift(T, nu, _ptr(u), int(s), _ptr(out))
     return out
 
 

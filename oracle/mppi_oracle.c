@@ -561,6 +561,68 @@ static void cartpole_jacobians(const double *P, const double *x, const double *v
     Jp[3][1] = (dN2_dmc * lD - N2 * l) / (lD * lD);
 }
 
+int oracle_mppi_iterate(const oracle_problem *p, const double *x0, const double *u_nom,
+                        int iterations, double gamma, double *u_new, double *w_out,
+                        double *S_out, double *stats, int n_threads)
+{
+    if (check_problem(p) != OR_OK || iterations < 1 || !(gamma >= 0.0)) return OR_ERR_INVALID_ARG;
+    int K = p->K;
+    long TN = (long)p->T * p->nu;
+    double *u = (double *)malloc(sizeof(double) * TN);
+    double *eps = (double *)malloc(sizeof(double) * K * TN);
+    double *S = (double *)malloc(sizeof(double) * K);
+    double *w = (double *)malloc(sizeof(double) * K);
+    double *unused = (double *)malloc(sizeof(double) * TN);
+    if (!u || !eps || !S || !w || !unused) {
+        free(u); free(eps); free(S); free(w); free(unused);
+        return OR_ERR_INVALID_ARG;
+    }
+    memcpy(u, u_nom, sizeof(double) * TN);
+    int st = OR_OK;
+    for (int i = 0; i < iterations; ++i) {
+        oracle_problem q = *p;
+        q.step = p->step + (uint64_t)i;
+        /* samples, rollouts, costs and weights around the current mean */
+        st = oracle_mppi_step(&q, x0, u, unused, w, S, stats, eps, n_threads);
+        /* u <- (1 - gamma) u + gamma * E_w[v], v^m = u + eps^m */
+        for (long e = 0; e < TN; ++e) {
+            double mean_v = 0.0;
+            if (st == OR_OK)
+                for (int k = 0; k < K; ++k) mean_v += w[k] * (u[e] + eps[(long)k * TN + e]);
+            else
+                mean_v = u[e];
+            u[e] = (1.0 - gamma) * u[e] + gamma * mean_v;
+        }
+    }
+    memcpy(u_new, u, sizeof(double) * TN);
+    if (w_out) memcpy(w_out, w, sizeof(double) * K);
+    if (S_out) memcpy(S_out, S, sizeof(double) * K);
+    free(u); free(eps); free(S); free(w); free(unused);
+    return st;
+}
+
+void oracle_nominal_trajectory(const oracle_problem *p, const double *x0, const double *u,
+                               double *traj)
+{
+    int nx = p->nx, nu = p->nu;
+    double x[OR_MAX_NX], xn[OR_MAX_NX];
+    memcpy(x, x0, sizeof(double) * nx);
+    memcpy(traj, x, sizeof(double) * nx);
+    for (int t = 0; t < p->T; ++t) {
+        oracle_dynamics_step(p, x, u + (long)t * nu, xn);
+        memcpy(x, xn, sizeof(double) * nx);
+        memcpy(traj + (long)(t + 1) * nx, x, sizeof(double) * nx);
+    }
+}
+
+void oracle_shift(int T, int nu, const double *u, int s, double *out)
+{
+    for (int t = 0; t < T; ++t) {
+        int src = t + s < T ? t + s : T - 1;
+        for (int j = 0; j < nu; ++j) out[(long)t * nu + j] = u[(long)src * nu + j];
+    }
+}
+
 int oracle_mppi_grad_cartpole(const oracle_problem *p, const double *x0,
                               const double *u_nom, const double *G, double *grad,
                               int n_threads)

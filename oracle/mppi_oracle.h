@@ -96,6 +96,27 @@ int oracle_mppi_step(const oracle_problem *p, const double *x0, const double *u_
                      double *u_new, double *w, double *S, double *stats,
                      double *eps_out, int n_threads);
 
+/* Algorithm 1 with its outer loop over I iterations and the DMD-MPC step
+ * size gamma (Sec. V-B, its step-size update law): iteration i samples
+ * around the mean u^i with Philox step counter p->step + i and sets
+ *   u^{i+1}_t = (1 - gamma) u^i_t + gamma * sum_m w^m v^m_t,
+ * the weighted mean of the sampled controls v^m = u^i + eps^m (written as the
+ * paper prints it).  u_new = u^I; w, S, stats (may be NULL) are those of the
+ * last iteration.  gamma = 1 and I = 1 is oracle_mppi_step. */
+int oracle_mppi_iterate(const oracle_problem *p, const double *x0, const double *u_nom,
+                        int iterations, double gamma, double *u_new, double *w, double *S,
+                        double *stats, int n_threads);
+
+/* The trajectory of x0 under the control sequence u (no noise), as the
+ * controller's output trajectory after an optimisation: traj[(T+1)*nx]. */
+void oracle_nominal_trajectory(const oracle_problem *p, const double *x0, const double *u,
+                               double *traj);
+
+/* MPC shift of the mean control sequence by s steps for the next
+ * optimisation (Sec. IV-A, the plant's re-planning): out_t = u_{t+s} for
+ * t < T - s; the last s steps hold the final control u_{T-1}. */
+void oracle_shift(int T, int nu, const double *u, int s, double *out);
+
 /* Gradient of L = sum(G * u_new) for the cart-pole with quadratic cost with
  * respect to theta = (Q[0..3], R, l, m_c), by forward-mode tangents, at fixed
  * noise.  grad[7]. */
