@@ -284,9 +284,9 @@ def time_steps_flushed(fn, steps, flush, warmup=3):
 
 
 def extensions(m, dev, peak_tflops, bf16_peak):
-    """The batched, differentiable and BF16-MLP forms on the same GPU, and
-    the quadrotor on a K sweep (where the FP32 roofline fraction is the
-    meaningful figure)."""
+    """The batched, differentiable, multi-iteration and BF16-MLP forms on the
+    same GPU, and the quadrotor on a K sweep (where the FP32 roofline fraction
+    is the meaningful figure)."""
     import torch
     out = {}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -340,6 +340,24 @@ def extensions(m, dev, peak_tflops, bf16_peak):
                                          "grads w.r.t. Q(4), R, l, m_c",
                              "forward_ms": ms_f, "forward_backward_ms": ms_fb,
                              "rollout_steps_per_s": p["K"] * p["T"] / (ms_fb * 1e-3)}
+    ctl.close()
+    # multi-iteration MPPI with the DMD-MPC step size (Algorithm 1's outer
+    # loop, Sec. V-B), the output trajectory and the MPC shift (Sec. IV-A)
+    p = W.quadrotor()
+    ctl = m.MPPI.from_problem(p)
+    x0 = torch.tensor(p["x0"], dtype=torch.float32, device=dev)
+    u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device=dev)
+    un = torch.empty_like(u)
+    rounds, gamma = 3, 0.5
+    ctl.set_iterations(rounds, gamma)
+    ms_it = time_steps_flushed(lambda: ctl.step_into(x0, u, un), 20, flush)
+    ms_traj = time_steps_flushed(lambda: ctl.nominal_trajectory(x0, un), 20, flush)
+    ms_shift = time_steps_flushed(lambda: ctl.shift(un, 1), 20, flush)
+    out["multi_iteration"] = {"workload": f"quadrotor K={p['K']} T={p['T']}, {rounds} rounds, "
+                                          f"step size {gamma}",
+                              "ms_per_step": ms_it, "ms_per_round": ms_it / rounds,
+                              "rollout_steps_per_s": rounds * p["K"] * p["T"] / (ms_it * 1e-3),
+                              "nominal_trajectory_ms": ms_traj, "shift_ms": ms_shift}
     ctl.close()
     # precision: bicycle + MLP, BF16 tensor cores vs FP32 CUDA cores
     p = W.bicycle_mlp()

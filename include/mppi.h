@@ -215,6 +215,38 @@ MPPI_API mppi_status mppi_set_params(mppi_ctx *ctx, const float *dyn_params, con
 MPPI_API mppi_status mppi_step_backward(mppi_ctx *ctx, const float *grad_u_new_d,
                                float *grad_params_d);
 
+/* Algorithm 1's outer loop and the DMD-MPC step size (Sec. V-B).  Each
+ * mppi_step then runs `iterations` rounds of sample, roll out, weigh and
+ * update; round i samples around the mean left by round i - 1 with step
+ * counter c + i (the counter advances by `iterations`) and moves the mean by
+ *   u <- (1 - gamma) u + gamma * sum_k w_k v_k = u + gamma * sum_k w_k eps_k
+ * (the weights sum to one).  weights, stats and costs are those of the last
+ * round.  iterations 1..1024 (default 1), step_size gamma >= 0 and finite
+ * (default 1, Algorithm 1's update; 0 leaves the mean unchanged).  The
+ * batched API and mppi_update_noalloc keep gamma = 1; mppi_step_backward
+ * needs iterations = 1 and gamma = 1 (MPPI_ERR_UNSUPPORTED otherwise).
+ * Errors: MPPI_ERR_INVALID_ARG for values out of range, MPPI_ERR_CUDA if the
+ * scratch for the intermediate means (2 T nu floats) cannot be allocated. */
+MPPI_API mppi_status mppi_set_iterations(mppi_ctx *ctx, int iterations, float step_size);
+
+/* The state trajectory of x0 under the control sequence u without noise,
+ * as the controller returns after an optimisation (Sec. IV-B: the output
+ * trajectory computed from the optimal control): traj_d[(T+1)*nx] =
+ * x0, F(x0, u_0), ... (row-major, device, overwritten).  x0_d [nx] and
+ * u_d [T*nu] are device pointers.  The dynamics are the context's, in FP32
+ * (BICYCLE_MLP runs its MLP in FP32 here at either precision).  Asynchronous
+ * on the context's stream; one thread integrates (T serial steps). */
+MPPI_API mppi_status mppi_nominal_trajectory(mppi_ctx *ctx, const float *x0_d, const float *u_d,
+                                             float *traj_d);
+
+/* MPC shift of the mean control sequence for the next optimisation
+ * (Sec. IV-A: the plant re-plans from the sequence advanced by the steps
+ * since the last optimisation): out_d[t*nu+j] = u_d[min(t+s, T-1)*nu+j], the
+ * last s steps holding the final control.  s >= 0; u_d and out_d [T*nu]
+ * device pointers that must not overlap (MPPI_ERR_INVALID_ARG otherwise).
+ * Asynchronous on the context's stream. */
+MPPI_API mppi_status mppi_shift(mppi_ctx *ctx, const float *u_d, int s, float *out_d);
+
 /* Step counter used as the noise counter's high words.  get synchronises the
  * stream (the counter lives on the device); set is ordered on the stream. */
 MPPI_API mppi_status mppi_get_counter(mppi_ctx *ctx, uint64_t *counter);

@@ -213,6 +213,35 @@ class MPPI:
         check(load().mppi_set_counter(self._h, int(value) & (2**64 - 1)), "mppi_set_counter",
               self._h)
 
+    def set_iterations(self, iterations: int, step_size: float = 1.0):
+        """Algorithm 1's outer loop and the DMD-MPC step size (Sec. V-B): each
+        step runs ``iterations`` rounds, moving the mean by
+        u <- (1 - step_size) u + step_size * (weighted mean of the samples)."""
+        check(load().mppi_set_iterations(self._h, int(iterations), float(step_size)),
+              "mppi_set_iterations", self._h)
+
+    def nominal_trajectory(self, x0, u, stream=None):
+        """States [T+1, nx] of x0 under the control sequence u, without noise."""
+        import torch
+        L = load()
+        _check_tensor(x0, self.nx, "x0")
+        _check_tensor(u, self.T * self.nu, "u")
+        traj = torch.empty((self.T + 1, self.nx), dtype=torch.float32, device=x0.device)
+        self._use_stream(L, stream)
+        check(L.mppi_nominal_trajectory(self._h, _dptr(x0), _dptr(u), _dptr(traj)),
+              "mppi_nominal_trajectory", self._h)
+        return traj
+
+    def shift(self, u, s: int, stream=None):
+        """The control sequence advanced by s steps, the last s holding u[T-1]."""
+        import torch
+        L = load()
+        _check_tensor(u, self.T * self.nu, "u")
+        out = torch.empty_like(u)
+        self._use_stream(L, stream)
+        check(L.mppi_shift(self._h, _dptr(u), int(s), _dptr(out)), "mppi_shift", self._h)
+        return out
+
     def profile(self, enable: bool):
         """Start (clearing the record) or stop per-kernel event timing."""
         check(load().mppi_profile(self._h, 1 if enable else 0), "mppi_profile", self._h)

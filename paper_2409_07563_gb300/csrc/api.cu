@@ -85,6 +85,7 @@ void free_ctx(mppi_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->io_host) cudaFreeHost(c->io_host);
+    if (c->u_iter) cudaFree(c->u_iter);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     void *ptrs[] = {c->d_dyn, c->d_cost, c->d_map, c->scr.S, c->scr.w, c->scr.nz, c->scr.cand,
                     c->scr.partials, c->scr.upartials,
@@ -177,6 +178,7 @@ StepParams make_params(const mppi_ctx &c) {
     p.dt = c.dt;
     p.lambda = c.lambda;
     p.lam_beta = c.beta ? c.lambda : 0.f;
+    p.gamma = c.gamma;
     for (int j = 0; j < c.nu; ++j) {
         p.sigma[j] = c.sigma[j];
         p.ivar[j] = c.sigma[j] > 0.f ? 1.0f / (c.sigma[j] * c.sigma[j]) : 0.f;
@@ -428,29 +430,36 @@ mppi_status mppi_step(mppi_ctx *ctx, const float *x0_d, const float *u_nom_d, fl
     if (!ctx) return MPPI_ERR_INVALID_ARG;
     if (!x0_d || !u_nom_d || !u_new_d)
         return fail(ctx, MPPI_ERR_INVALID_ARG, "x0, u_nom and u_new must be device pointers");
-    StepParams p = make_params(*ctx);
-    p.x0 = x0_d;
-    p.u_nom = u_nom_d;
-    p.u_new = u_new_d;
-    p.weights_out = weights_d;
-    p.stats_out = stats_d;
-    p.costs_out = costs_d;
-    cudaError_t e;
-    {
-        ProfScope ps(ctx, MPPI_PROF_ROLLOUT);
-        e = ctx->plan.variant == mppi::kVariantQuadGroup ? mppi::launch_quad_group(*ctx, p)
-            : ctx->plan.variant == mppi::kVariantQuadSplit ? mppi::launch_quad_split(*ctx, p)
-            : ctx->plan.variant == mppi::kVariantQuadPair ? mppi::launch_quad_pair(*ctx, p)
-            : ctx->plan.variant == mppi::kVariantMlpBf16 ? mppi::launch_mlp_bf16(*ctx, p)
-            : ctx->plan.variant == mppi::kVariantMlpF32 ? mppi::launch_mlp_f32(*ctx, p)
-                                                         : mppi::launch_rollout(*ctx, p);
+    const size_t TN = static_cast<size_t>(ctx->T) * ctx->nu;
+    // Algorithm 1's outer loop: round i samples around the mean of round
+    // i - 1 (ping-pong through u_iter); only the last round writes the
+    // caller's outputs.  The kernels advance the step counter once per round.
+    for (int it = 0; it < ctx->iterations; ++it) {
+        const bool last = it == ctx->iterations - 1;
+        StepParams p = make_params(*ctx);
+        p.x0 = x0_d;
+        p.u_nom = it == 0 ? u_nom_d : ctx->u_iter + ((it - 1) & 1) * TN;
+        p.u_new = last ? u_new_d : ctx->u_iter + (it & 1) * TN;
+        p.weights_out = last ? weights_d : nullptr;
+        p.stats_out = last ? stats_d : nullptr;
+        p.costs_out = last ? costs_d : nullptr;
+        cudaError_t e;
+        {
+            ProfScope ps(ctx, MPPI_PROF_ROLLOUT);
+            e = ctx->plan.variant == mppi::kVariantQuadGroup ? mppi::launch_quad_group(*ctx, p)
+                : ctx->plan.variant == mppi::kVariantQuadSplit ? mppi::launch_quad_split(*ctx, p)
+                : ctx->plan.variant == mppi::kVariantQuadPair ? mppi::launch_quad_pair(*ctx, p)
+                : ctx->plan.variant == mppi::kVariantMlpBf16 ? mppi::launch_mlp_bf16(*ctx, p)
+                : ctx->plan.variant == mppi::kVariantMlpF32 ? mppi::launch_mlp_f32(*ctx, p)
+                                                             : mppi::launch_rollout(*ctx, p);
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "rollout launch");
+        {
+            ProfScope ps(ctx, MPPI_PROF_UPDATE);
+            e = mppi::launch_update(*ctx, p);
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "update launch");
     }
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "rollout launch");
-    {
-        ProfScope ps(ctx, MPPI_PROF_UPDATE);
-        e = mppi::launch_update(*ctx, p);
-    }
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "update launch");
     ctx->have_step = true;
     ctx->err.clear();
     return MPPI_OK;
@@ -523,6 +532,9 @@ mppi_status mppi_step_backward(mppi_ctx *ctx, const float *grad_u_new_d, float *
         return fail(ctx, MPPI_ERR_UNSUPPORTED,
                     "backward needs CARTPOLE dynamics, QUADRATIC cost and EULER");
     if (!ctx->have_step) return fail(ctx, MPPI_ERR_UNSUPPORTED, "backward needs a prior mppi_step");
+    if (ctx->iterations != 1 || ctx->gamma != 1.f)
+        return fail(ctx, MPPI_ERR_UNSUPPORTED,
+                    "backward differentiates one plain iteration (iterations 1, step size 1)");
     if (!grad_u_new_d || !grad_params_d)
         return fail(ctx, MPPI_ERR_INVALID_ARG, "grad_u_new and grad_params must be device pointers");
     cudaError_t e;
@@ -543,6 +555,41 @@ mppi_status mppi_step_backward(mppi_ctx *ctx, const float *grad_u_new_d, float *
                                  ctx->stream);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
+    return MPPI_OK;
+}
+
+mppi_status mppi_set_iterations(mppi_ctx *ctx, int iterations, float step_size) {
+    if (!ctx) return MPPI_ERR_INVALID_ARG;
+    if (iterations < 1 || iterations > 1024 || !std::isfinite(step_size) || !(step_size >= 0.f))
+        return fail(ctx, MPPI_ERR_INVALID_ARG, "iterations 1..1024 and a finite step size >= 0");
+    if (iterations > 1 && !ctx->u_iter) {
+        cudaError_t e = dalloc(&ctx->u_iter, 2 * static_cast<size_t>(ctx->T) * ctx->nu);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "iteration scratch allocation");
+    }
+    ctx->iterations = iterations;
+    ctx->gamma = step_size;
+    return MPPI_OK;
+}
+
+mppi_status mppi_nominal_trajectory(mppi_ctx *ctx, const float *x0_d, const float *u_d,
+                                    float *traj_d) {
+    if (!ctx) return MPPI_ERR_INVALID_ARG;
+    if (!x0_d || !u_d || !traj_d)
+        return fail(ctx, MPPI_ERR_INVALID_ARG, "x0, u and traj must be device pointers");
+    cudaError_t e = mppi::launch_nominal_trajectory(*ctx, x0_d, u_d, traj_d);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "trajectory launch");
+    return MPPI_OK;
+}
+
+mppi_status mppi_shift(mppi_ctx *ctx, const float *u_d, int s, float *out_d) {
+    if (!ctx) return MPPI_ERR_INVALID_ARG;
+    if (!u_d || !out_d || s < 0)
+        return fail(ctx, MPPI_ERR_INVALID_ARG, "u and out must be device pointers, s >= 0");
+    const size_t TN = static_cast<size_t>(ctx->T) * ctx->nu;
+    if (u_d < out_d + TN && out_d < u_d + TN)
+        return fail(ctx, MPPI_ERR_INVALID_ARG, "u and out must not overlap");
+    cudaError_t e = mppi::launch_shift(*ctx, u_d, s, out_d);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "shift launch");
     return MPPI_OK;
 }
 

@@ -48,6 +48,7 @@ struct Scratch {
 struct StepParams {
     int K, T, nx, nu;
     float dt, lambda, lam_beta;        // lam_beta = beta * lambda
+    float gamma;                       // step size of the mean update (1: plain MPPI)
     float sigma[kMaxNu], ivar[kMaxNu];  // ivar = 1/sigma^2 (0 where sigma = 0)
     uint64_t seed;
     const float *x0, *u_nom;
@@ -107,6 +108,9 @@ struct mppi_ctx {
     int device = 0, num_sms = 0;
     bool have_step = false;
     bool differentiable = false;        // cart-pole + quadratic + Euler
+    int iterations = 1;                 // Algorithm 1's outer loop
+    float gamma = 1.f;                  // DMD-MPC step size of the mean update
+    float *u_iter = nullptr;            // [2 T nu] means between iterations (iterations > 1)
     std::string err;
     ProfileRecord prof;
 };
@@ -119,6 +123,11 @@ size_t rollout_smem_bytes(const mppi_ctx &c);
 cudaError_t rollout_prepare(const mppi_ctx &c);  // sets smem attributes
 cudaError_t launch_rollout(const mppi_ctx &c, const StepParams &p);
 cudaError_t launch_update(const mppi_ctx &c, const StepParams &p);
+// the state trajectory of x0 under u (no noise): traj[(T+1) nx]
+cudaError_t launch_nominal_trajectory(const mppi_ctx &c, const float *x0, const float *u,
+                                      float *traj);
+// out[t] = u[min(t + s, T - 1)]
+cudaError_t launch_shift(const mppi_ctx &c, const float *u, int s, float *out);
 cudaError_t launch_sample_noise(uint64_t seed, uint64_t step, int K, int Q, uint32_t *bits,
                                 float *z, cudaStream_t s);
 cudaError_t launch_store_u64(unsigned long long *dst, unsigned long long v, cudaStream_t s);

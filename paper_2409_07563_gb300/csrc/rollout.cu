@@ -104,7 +104,61 @@ bool dispatch(int dyn, int cost, int nx, int nu, F &&f) {
     }
 }
 
+// The state trajectory of x0 under u without noise (the controller's output
+// trajectory after an optimisation): the block stages the model parameters,
+// one thread steps the model T times (the same Dyn::step as the rollout).
+template <class Dyn>
+__global__ void nominal_trajectory_kernel(const float *dyn_params, const float *x0,
+                                          const float *u, float *traj, int T, float dt) {
+    extern __shared__ __align__(16) float smem[];
+    Dyn::prepare(dyn_params, smem, threadIdx.x, blockDim.x);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    float x[Dyn::NX];
+#pragma unroll
+    for (int i = 0; i < Dyn::NX; ++i) {
+        x[i] = x0[i];
+        traj[i] = x[i];
+    }
+    for (int t = 0; t < T; ++t) {
+        float v[Dyn::NU];
+#pragma unroll
+        for (int j = 0; j < Dyn::NU; ++j) v[j] = u[t * Dyn::NU + j];
+        Dyn::step(x, v, smem, dt);
+#pragma unroll
+        for (int i = 0; i < Dyn::NX; ++i) traj[(t + 1) * Dyn::NX + i] = x[i];
+    }
+}
+
+__global__ void shift_kernel(const float *u, int T, int nu, int s, float *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T * nu) return;
+    const int t = i / nu, j = i % nu;
+    const int src = t + s < T ? t + s : T - 1;  // s >= 0 (checked by the caller)
+    out[i] = u[src * nu + j];
+}
+
 }  // namespace
+
+cudaError_t launch_nominal_trajectory(const mppi_ctx &c, const float *x0, const float *u,
+                                      float *traj) {
+    cudaError_t err = cudaErrorInvalidValue;
+    dispatch(c.dyn_kind, c.cost_kind, c.nx, c.nu, [&](auto *d, auto *) {
+        using D = std::remove_pointer_t<decltype(d)>;
+        const size_t smem = sizeof(float) * round_up4(D::smem_floats(
+                                                static_cast<int>(c.dyn_params_h.size())));
+        nominal_trajectory_kernel<D><<<1, 128, smem, c.stream>>>(c.d_dyn, x0, u, traj, c.T, c.dt);
+        err = cudaGetLastError();
+        return true;
+    });
+    return err;
+}
+
+cudaError_t launch_shift(const mppi_ctx &c, const float *u, int s, float *out) {
+    const int n = c.T * c.nu;
+    shift_kernel<<<(n + 255) / 256, 256, 0, c.stream>>>(u, c.T, c.nu, s, out);
+    return cudaGetLastError();
+}
 
 bool rollout_supported(int dyn_kind, int cost_kind, int nx, int nu) {
     return dispatch(dyn_kind, cost_kind, nx, nu, [](auto *d, auto *) {

@@ -224,7 +224,7 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, int ca
             for (int i = 0; i < 4; ++i) {
                 if (t0 + i < p.T) {
                     const int o = (t0 + i) * p.nu + j;
-                    p.u_new[o] = un[o] + acc[i];
+                    p.u_new[o] = un[o] + p.gamma * acc[i];
                 }
             }
         }

@@ -1,7 +1,9 @@
 // update.cu -- weighted control update (step a5) and the noise diagnostic.
 //
-// u_new[t, j] = u_nom[t, j] + sum_k w_k eps_{k,t,j} for every (t, j)
-// (Algorithm 1, control update), over the samples with non-zero weight that
+// u_new[t, j] = u_nom[t, j] + gamma sum_k w_k eps_{k,t,j} for every (t, j)
+// (Algorithm 1, control update, at gamma = 1; otherwise the DMD-MPC step size
+// of Sec. V-B: (1 - gamma) u + gamma * (weighted mean of v), the weights
+// summing to one), over the samples with non-zero weight that
 // the rollout's last block listed (a weight that underflowed to zero
 // contributes exactly zero).  eps is regenerated from the same Philox counter
 // the rollout used (bit-identical FP32 product sigma_j * z), never read from
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
         for (int c = 0; c < static_cast<int>(gridDim.y); ++c)
             sum += __ldcg(p.upartials + (static_cast<size_t>(c) * Q) * 4 + el);
         const int o = t * NU + j;
-        p.u_new[o] = p.u_nom[o] + sum;
+        p.u_new[o] = p.u_nom[o] + p.gamma * sum;  // gamma = 1: u_nom + sum exactly
     }
     if (threadIdx.x == 0) {
         const unsigned long long step = *p.counter;
