@@ -88,6 +88,8 @@ def lib():
         L.oracle_nominal_trajectory.restype = None
         L.oracle_shift.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp]
         L.oracle_shift.restype = None
+        L.oracle_cem_weights.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp]
+        L.oracle_cem_step.argtypes = [P, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, ctypes.c_int]
         L.oracle_max_threads.argtypes = []
     return _lib
 
@@ -262,6 +264,29 @@ def shift(u, s):
     out = np.zeros_like(u)
     lib().oracle_shift(T, nu, _ptr(u), int(s), _ptr(out))
     return out
+
+
+def cem_weights(S, n_elite):
+    """Elite-set weights (1/|E| on the n_elite lowest costs, ties included)
+    and |E| (-1 for bad arguments)."""
+    S = np.ascontiguousarray(S, float)
+    w = np.zeros(len(S))
+    n = lib().oracle_cem_weights(len(S), _ptr(S), int(n_elite), _ptr(w))
+    return w, n
+
+
+def cem_step(p, top_k_fraction, step=0, n_threads=1, x0=None, u_nom=None):
+    """One CEM iteration; returns dict(u_new, w, S, status)."""
+    P = Problem(p, step)
+    K, T, nu = p["K"], p["T"], p["nu"]
+    x0 = np.ascontiguousarray(p["x0"] if x0 is None else x0, float)
+    u = np.ascontiguousarray(p["u_nom"] if u_nom is None else u_nom, float)
+    u_new = np.zeros((T, nu))
+    w = np.zeros(K)
+    S = np.zeros(K)
+    st = lib().oracle_cem_step(P.ref, _ptr(x0), _ptr(u), float(top_k_fraction), _ptr(u_new),
+                               _ptr(w), _ptr(S), int(n_threads))
+    return dict(u_new=u_new, w=w, S=S, status=st)
 
 
 def mppi_grad_cartpole(p, G, step=0, n_threads=1, x0=None, u_nom=None):

@@ -623,6 +623,68 @@ void oracle_shift(int T, int nu, const double *u, int s, double *out)
     }
 }
 
+/* total order of costs: finite ascending, then +inf, then NaN */
+static int cost_cmp(double a, double b)
+{
+    int an = isnan(a), bn = isnan(b);
+    if (an || bn) return an - bn;
+    return (a > b) - (a < b);
+}
+
+static int cost_cmp_qsort(const void *x, const void *y)
+{
+    return cost_cmp(*(const double *)x, *(const double *)y);
+}
+
+int oracle_cem_weights(int K, const double *S, int n_elite, double *w)
+{
+    if (K <= 0 || n_elite < 1 || n_elite > K || !S || !w) return -1;
+    double *sorted = (double *)malloc(sizeof(double) * K);
+    if (!sorted) return -1;
+    memcpy(sorted, S, sizeof(double) * K);
+    qsort(sorted, K, sizeof(double), cost_cmp_qsort);
+    double tau = sorted[n_elite - 1];
+    free(sorted);
+    int n = 0;
+    for (int k = 0; k < K; ++k) n += cost_cmp(S[k], tau) <= 0;
+    for (int k = 0; k < K; ++k) w[k] = cost_cmp(S[k], tau) <= 0 ? 1.0 / n : 0.0;
+    return n;
+}
+
+int oracle_cem_step(const oracle_problem *p, const double *x0, const double *u_nom,
+                    double top_k_fraction, double *u_new, double *w_out, double *S_out,
+                    int n_threads)
+{
+    if (check_problem(p) != OR_OK || !(top_k_fraction > 0.0) || top_k_fraction > 1.0)
+        return OR_ERR_INVALID_ARG;
+    int K = p->K;
+    long TN = (long)p->T * p->nu;
+    double *eps = (double *)malloc(sizeof(double) * K * TN);
+    double *S = (double *)malloc(sizeof(double) * K);
+    double *w = (double *)malloc(sizeof(double) * K);
+    double *unused = (double *)malloc(sizeof(double) * TN);
+    if (!eps || !S || !w || !unused) {
+        free(eps); free(S); free(w); free(unused);
+        return OR_ERR_INVALID_ARG;
+    }
+    /* the same samples, rollouts and costs as an MPPI iteration */
+    oracle_mppi_step(p, x0, u_nom, unused, NULL, S, NULL, eps, n_threads);
+    int n_elite = (int)floor((double)K * top_k_fraction);
+    if (n_elite < 1) n_elite = 1;
+    oracle_cem_weights(K, S, n_elite, w);
+    /* the new mean: the elite samples' average control */
+    for (long e = 0; e < TN; ++e) {
+        double acc = 0.0;
+        for (int k = 0; k < K; ++k)
+            if (w[k] != 0.0) acc += w[k] * eps[(long)k * TN + e];
+        u_new[e] = u_nom[e] + acc;
+    }
+    if (w_out) memcpy(w_out, w, sizeof(double) * K);
+    if (S_out) memcpy(S_out, S, sizeof(double) * K);
+    free(eps); free(S); free(w); free(unused);
+    return OR_OK;
+}
+
 int oracle_mppi_grad_cartpole(const oracle_problem *p, const double *x0,
                               const double *u_nom, const double *G, double *grad,
                               int n_threads)

@@ -117,6 +117,21 @@ void oracle_nominal_trajectory(const oracle_problem *p, const double *x0, const 
  * t < T - s; the last s steps hold the final control u_{T-1}. */
 void oracle_shift(int T, int nu, const double *u, int s, double *out);
 
+/* Elite-set weights of the cross-entropy method controller (the paper's CEM
+ * controller example, Sec. IV-C: keep the top_k_percentage lowest-cost
+ * samples, zero the rest, recompute the mean).  Reading: the threshold tau is
+ * the n_elite-th smallest cost in the total order finite < +inf < NaN; the
+ * elite set is every sample with S_k <= tau (ties at tau included), each
+ * weighted 1/|E|.  w[K]; returns |E|, or -1 for bad arguments. */
+int oracle_cem_weights(int K, const double *S, int n_elite, double *w);
+
+/* One CEM iteration: the MPPI sampling and rollouts (same noise and costs),
+ * then u_new = u_nom + sum_k w_k eps_k with the elite-set weights, n_elite =
+ * max(1, floor(K * top_k_fraction)), 0 < top_k_fraction <= 1.  w, S may be
+ * NULL.  Returns OR_OK or OR_ERR_INVALID_ARG. */
+int oracle_cem_step(const oracle_problem *p, const double *x0, const double *u_nom,
+                    double top_k_fraction, double *u_new, double *w, double *S, int n_threads);
+
 /* Gradient of L = sum(G * u_new) for the cart-pole with quadratic cost with
  * respect to theta = (Q[0..3], R, l, m_c), by forward-mode tangents, at fixed
  * noise.  grad[7]. */
