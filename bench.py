@@ -284,7 +284,7 @@ def time_steps_flushed(fn, steps, flush, warmup=3):
 
 
 def extensions(m, dev, peak_tflops, bf16_peak):
-    """The batched, differentiable, multi-iteration and BF16-MLP forms on the
+    """The batched, differentiable, multi-iteration, CEM and BF16-MLP forms on the
     same GPU, and the quadrotor on a K sweep (where the FP32 roofline fraction
     is the meaningful figure)."""
     import torch
@@ -358,6 +358,20 @@ def extensions(m, dev, peak_tflops, bf16_peak):
                               "ms_per_step": ms_it, "ms_per_round": ms_it / rounds,
                               "rollout_steps_per_s": rounds * p["K"] * p["T"] / (ms_it * 1e-3),
                               "nominal_trajectory_ms": ms_traj, "shift_ms": ms_shift}
+    ctl.close()
+    # CEM elite-set weights (Sec. IV-C) on the same workload, one round
+    ctl = m.MPPI.from_problem(p)
+    ctl.set_cem(0.1)
+    ms_cem = time_steps_flushed(lambda: ctl.step_into(x0, u, un), 20, flush)
+    ctl.profile(True)
+    for _ in range(10):
+        ctl.step_into(x0, u, un)
+    prof = ctl.profile_read()
+    ctl.profile(False)
+    out["cem"] = {"workload": f"quadrotor K={p['K']} T={p['T']}, elite fraction 0.1",
+                  "ms_per_step": ms_cem,
+                  "rollout_steps_per_s": p["K"] * p["T"] / (ms_cem * 1e-3),
+                  "elite_select_ms": prof["other"][0] / max(1, prof["other"][1])}
     ctl.close()
     # precision: bicycle + MLP, BF16 tensor cores vs FP32 CUDA cores
     p = W.bicycle_mlp()

@@ -229,6 +229,18 @@ MPPI_API mppi_status mppi_step_backward(mppi_ctx *ctx, const float *grad_u_new_d
  * scratch for the intermediate means (2 T nu floats) cannot be allocated. */
 MPPI_API mppi_status mppi_set_iterations(mppi_ctx *ctx, int iterations, float step_size);
 
+/* Cross-entropy method weights instead of MPPI's (the paper's CEM
+ * controller example, Sec. IV-C, parameter top_k_percentage): each round
+ * keeps the n = max(1, floor(K * top_k_fraction)) lowest-cost samples --
+ * every sample whose cost is <= the n-th smallest, ties included, in the
+ * order finite < +inf < NaN -- weighted 1/|E|, the others 0, and moves the
+ * mean to u + gamma * sum_k w_k eps_k (the elites' average control at
+ * gamma = 1).  top_k_fraction in (0, 1]; 0 returns to MPPI weights.  With
+ * CEM, weights_d receives the elite weights; stats_d stays MPPI's
+ * [F, rho, eta, ESS] of the same costs.  mppi_step_backward refuses CEM
+ * contexts (MPPI_ERR_UNSUPPORTED).  MPPI_ERR_INVALID_ARG outside [0, 1]. */
+MPPI_API mppi_status mppi_set_cem(mppi_ctx *ctx, float top_k_fraction);
+
 /* The state trajectory of x0 under the control sequence u without noise,
  * as the controller returns after an optimisation (Sec. IV-B: the output
  * trajectory computed from the optimal control): traj_d[(T+1)*nx] =
@@ -264,10 +276,16 @@ MPPI_API const char *mppi_last_error(const mppi_ctx *ctx);
  * every launch the context makes while profiling is on.  mppi_profile(ctx, 1)
  * clears the record and starts recording, mppi_profile(ctx, 0) stops.
  * mppi_profile_read() synchronises the stream and returns, per kernel slot
- * (MPPI_PROF_ROLLOUT, MPPI_PROF_UPDATE, MPPI_PROF_ADJOINT), the summed
- * elapsed milliseconds and the number of launches (arrays of
- * MPPI_PROF_SLOTS entries; either may be NULL). */
-enum { MPPI_PROF_ROLLOUT = 0, MPPI_PROF_UPDATE = 1, MPPI_PROF_ADJOINT = 2, MPPI_PROF_SLOTS = 4 };
+ * (MPPI_PROF_ROLLOUT, MPPI_PROF_UPDATE, MPPI_PROF_ADJOINT, MPPI_PROF_OTHER:
+ * the CEM elite-set selection), the summed elapsed milliseconds and the
+ * number of launches (arrays of MPPI_PROF_SLOTS entries; either may be NULL). */
+enum {
+    MPPI_PROF_ROLLOUT = 0,
+    MPPI_PROF_UPDATE = 1,
+    MPPI_PROF_ADJOINT = 2,
+    MPPI_PROF_OTHER = 3,
+    MPPI_PROF_SLOTS = 4
+};
 MPPI_API mppi_status mppi_profile(mppi_ctx *ctx, int enable);
 MPPI_API mppi_status mppi_profile_read(mppi_ctx *ctx, float *ms, int *launches);
 

@@ -220,6 +220,11 @@ class MPPI:
         check(load().mppi_set_iterations(self._h, int(iterations), float(step_size)),
               "mppi_set_iterations", self._h)
 
+    def set_cem(self, top_k_fraction: float):
+        """Cross-entropy-method weights (the lowest-cost fraction of the samples,
+        equally weighted) instead of MPPI's; 0 returns to MPPI."""
+        check(load().mppi_set_cem(self._h, float(top_k_fraction)), "mppi_set_cem", self._h)
+
     def nominal_trajectory(self, x0, u, stream=None):
         """States [T+1, nx] of x0 under the control sequence u, without noise."""
         import torch

@@ -91,11 +91,12 @@ def load() -> ctypes.CDLL:
     L.mppi_set_iterations.argtypes = [vp, i, ctypes.c_float]
     L.mppi_nominal_trajectory.argtypes = [vp, vp, vp, vp]
     L.mppi_shift.argtypes = [vp, vp, i, vp]
+    L.mppi_set_cem.argtypes = [vp, ctypes.c_float]
     for name in ("mppi_create", "mppi_set_stream", "mppi_step", "mppi_step_host",
                  "mppi_set_params", "mppi_step_backward", "mppi_get_counter",
                  "mppi_set_counter", "mppi_poll_status", "mppi_sample_noise", "mppi_profile",
                  "mppi_profile_read", "mppi_set_iterations", "mppi_nominal_trajectory",
-                 "mppi_shift"):
+                 "mppi_shift", "mppi_set_cem"):
         getattr(L, name).restype = ctypes.c_int
     _optional(L)
     _lib = L

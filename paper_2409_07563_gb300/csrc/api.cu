@@ -179,6 +179,7 @@ StepParams make_params(const mppi_ctx &c) {
     p.lambda = c.lambda;
     p.lam_beta = c.beta ? c.lambda : 0.f;
     p.gamma = c.gamma;
+    p.n_elite = c.n_elite;
     for (int j = 0; j < c.nu; ++j) {
         p.sigma[j] = c.sigma[j];
         p.ivar[j] = c.sigma[j] > 0.f ? 1.0f / (c.sigma[j] * c.sigma[j]) : 0.f;
@@ -454,6 +455,11 @@ mppi_status mppi_step(mppi_ctx *ctx, const float *x0_d, const float *u_nom_d, fl
                                                              : mppi::launch_rollout(*ctx, p);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "rollout launch");
+        if (ctx->n_elite > 0) {  // CEM: the elite set replaces the MPPI weights
+            ProfScope ps(ctx, MPPI_PROF_OTHER);
+            e = mppi::launch_cem_select(*ctx, p);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "elite-set launch");
+        }
         {
             ProfScope ps(ctx, MPPI_PROF_UPDATE);
             e = mppi::launch_update(*ctx, p);
@@ -532,9 +538,10 @@ mppi_status mppi_step_backward(mppi_ctx *ctx, const float *grad_u_new_d, float *
         return fail(ctx, MPPI_ERR_UNSUPPORTED,
                     "backward needs CARTPOLE dynamics, QUADRATIC cost and EULER");
     if (!ctx->have_step) return fail(ctx, MPPI_ERR_UNSUPPORTED, "backward needs a prior mppi_step");
-    if (ctx->iterations != 1 || ctx->gamma != 1.f)
+    if (ctx->iterations != 1 || ctx->gamma != 1.f || ctx->n_elite != 0)
         return fail(ctx, MPPI_ERR_UNSUPPORTED,
-                    "backward differentiates one plain iteration (iterations 1, step size 1)");
+                    "backward differentiates one plain MPPI iteration (iterations 1, step size 1, "
+                    "no CEM)");
     if (!grad_u_new_d || !grad_params_d)
         return fail(ctx, MPPI_ERR_INVALID_ARG, "grad_u_new and grad_params must be device pointers");
     cudaError_t e;
@@ -568,6 +575,19 @@ mppi_status mppi_set_iterations(mppi_ctx *ctx, int iterations, float step_size) 
     }
     ctx->iterations = iterations;
     ctx->gamma = step_size;
+    return MPPI_OK;
+}
+
+mppi_status mppi_set_cem(mppi_ctx *ctx, float top_k_fraction) {
+    if (!ctx) return MPPI_ERR_INVALID_ARG;
+    if (!std::isfinite(top_k_fraction) || top_k_fraction < 0.f || top_k_fraction > 1.f)
+        return fail(ctx, MPPI_ERR_INVALID_ARG, "top_k_fraction in [0, 1]");
+    if (top_k_fraction == 0.f) {
+        ctx->n_elite = 0;
+        return MPPI_OK;
+    }
+    const double n = std::floor(static_cast<double>(ctx->K) * static_cast<double>(top_k_fraction));
+    ctx->n_elite = std::max(1, static_cast<int>(n));
     return MPPI_OK;
 }
 

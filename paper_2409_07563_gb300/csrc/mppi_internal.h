@@ -49,6 +49,7 @@ struct StepParams {
     int K, T, nx, nu;
     float dt, lambda, lam_beta;        // lam_beta = beta * lambda
     float gamma;                       // step size of the mean update (1: plain MPPI)
+    int n_elite;                       // > 0: CEM elite-set weights instead of MPPI's
     float sigma[kMaxNu], ivar[kMaxNu];  // ivar = 1/sigma^2 (0 where sigma = 0)
     uint64_t seed;
     const float *x0, *u_nom;
@@ -111,6 +112,7 @@ struct mppi_ctx {
     int iterations = 1;                 // Algorithm 1's outer loop
     float gamma = 1.f;                  // DMD-MPC step size of the mean update
     float *u_iter = nullptr;            // [2 T nu] means between iterations (iterations > 1)
+    int n_elite = 0;                    // CEM elite-set size (0: MPPI weights)
     std::string err;
     ProfileRecord prof;
 };
@@ -128,6 +130,8 @@ cudaError_t launch_nominal_trajectory(const mppi_ctx &c, const float *x0, const 
                                       float *traj);
 // out[t] = u[min(t + s, T - 1)]
 cudaError_t launch_shift(const mppi_ctx &c, const float *u, int s, float *out);
+// cem.cu: elite-set weights (list for the update kernel)
+cudaError_t launch_cem_select(const mppi_ctx &c, const StepParams &p);
 cudaError_t launch_sample_noise(uint64_t seed, uint64_t step, int K, int Q, uint32_t *bits,
                                 float *z, cudaStream_t s);
 cudaError_t launch_store_u64(unsigned long long *dst, unsigned long long v, cudaStream_t s);

@@ -204,7 +204,9 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, int ca
     const int QT = (p.T + 3) / 4, Q = p.nu * QT;
     const int per_thread = (Q + nt - 1) / nt;
     // (per_thread >= 1, so an inline list has at most kInlineUpdateCalls entries)
-    const bool inline_update = list_mode && nnz * per_thread <= kInlineUpdateCalls;
+    // (CEM replaces the weights after this kernel: no inline update then)
+    const bool inline_update =
+        p.n_elite == 0 && list_mode && nnz * per_thread <= kInlineUpdateCalls;
     if (inline_update) {
         const NoiseKey nk = make_noise_key(p.seed, step);
         const float *un = s_unom ? s_unom : p.u_nom;  // the block's shared copy when it has one

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
     const float rho = p.scalars[0], eta = p.scalars[1];
     const bool valid = p.scalars[4] != 0.f;
     const int kchunk = (p.K + gridDim.y - 1) / gridDim.y;
-    if (p.weights_out && blockIdx.x == 0) {
+    if (p.weights_out && p.n_elite == 0 && blockIdx.x == 0) {  // CEM: written by its select
         const int k_end = min(p.K, (blockIdx.y + 1) * kchunk);
         for (int k = blockIdx.y * kchunk + threadIdx.x; k < k_end; k += blockDim.x) {
             const float S = p.S[k];
