@@ -207,12 +207,25 @@ static void deriv_bicycle(const double *P, const double *x, const double *v, dou
     xd[6] = r[3];
 }
 
+/* Differential drive of the paper's benchmark (Sec. V, Table of algorithm
+ * parameters): state [x, y, theta], control [v, omega], each clamped to its
+ * limits P = [v_min, v_max, w_min, w_max] before it acts. */
+static void deriv_diff_drive(const double *P, const double *x, const double *v, double *xd)
+{
+    double vc = v[0] < P[0] ? P[0] : v[0] > P[1] ? P[1] : v[0];
+    double wc = v[1] < P[2] ? P[2] : v[1] > P[3] ? P[3] : v[1];
+    xd[0] = vc * cos(x[2]);
+    xd[1] = vc * sin(x[2]);
+    xd[2] = wc;
+}
+
 int oracle_deriv(const oracle_problem *p, const double *x, const double *v, double *xd)
 {
     switch (p->dyn_kind) {
     case OR_DYN_CARTPOLE: deriv_cartpole(p->dyn_params, x, v, xd); return OR_OK;
     case OR_DYN_QUADROTOR: deriv_quadrotor(p->dyn_params, x, v, xd); return OR_OK;
     case OR_DYN_BICYCLE_MLP: deriv_bicycle(p->dyn_params, x, v, xd); return OR_OK;
+    case OR_DYN_DIFF_DRIVE: deriv_diff_drive(p->dyn_params, x, v, xd); return OR_OK;
     case OR_DYN_DOUBLE_INTEGRATOR:
         xd[0] = x[2]; xd[1] = x[3]; xd[2] = v[0]; xd[3] = v[1];
         return OR_OK;
@@ -316,10 +329,9 @@ static int crash_fp32(const double *obs, int n_obs, const double *y)
     return 0;
 }
 
-double oracle_costmap_sample(const oracle_problem *p, double x, double y)
+static double map_bilinear(const oracle_problem *p, double x, double y, double x_min,
+                           double y_min, double cell)
 {
-    const double *C = p->cost_params;
-    double x_min = C[3], y_min = C[4], cell = C[5];
     int W = p->map_w, H = p->map_h;
     /* continuous cell coordinates, cell centres at integers */
     double gx = (x - x_min) / cell - 0.5;
@@ -336,6 +348,26 @@ double oracle_costmap_sample(const oracle_problem *p, double x, double y)
     double top = (1.0 - fx) * m[(long)i0 * W + j0] + fx * m[(long)i0 * W + j0 + 1];
     double bot = (1.0 - fx) * m[(long)(i0 + 1) * W + j0] + fx * m[(long)(i0 + 1) * W + j0 + 1];
     return (1.0 - fy) * top + fy * bot;
+}
+
+double oracle_costmap_sample(const oracle_problem *p, double x, double y)
+{
+    const double *C = p->cost_params;
+    if (p->cost_kind == OR_COST_GOAL_COSTMAP) return map_bilinear(p, x, y, C[6], C[7], C[8]);
+    return map_bilinear(p, x, y, C[3], C[4], C[5]);
+}
+
+/* Goal position, goal angle and costmap obstacle cost of the paper's
+ * benchmark (Sec. V, Table of algorithm parameters): params
+ * [c_goal, c_angle, c_obs, gx, gy, g_theta, x_min, y_min, cell]:
+ * c_goal |p - g|^2 + c_angle wrap(theta - g_theta)^2 + c_obs M(x, y), with
+ * wrap into [-pi, pi] and M bilinear as for COSTMAP_SPEED. */
+static double goal_costmap_cost(const oracle_problem *p, const double *y)
+{
+    const double *C = p->cost_params;
+    double dx = y[0] - C[3], dy = y[1] - C[4];
+    double da = remainder(y[2] - C[5], 6.283185307179586476925);  /* 2 pi */
+    return C[0] * (dx * dx + dy * dy) + C[1] * da * da + C[2] * map_bilinear(p, y[0], y[1], C[6], C[7], C[8]);
 }
 
 static double circle_cost(const double *C, const double *y)
@@ -373,6 +405,8 @@ double oracle_running_cost(const oracle_problem *p, const double *y, const doubl
     }
     case OR_COST_CIRCLE:
         return circle_cost(C, y);
+    case OR_COST_GOAL_COSTMAP:
+        return goal_costmap_cost(p, y);
     default:
         return NAN;
     }
@@ -391,6 +425,8 @@ double oracle_terminal_cost(const oracle_problem *p, const double *y)
     }
     case OR_COST_CIRCLE:
         return 0.0;
+    case OR_COST_GOAL_COSTMAP:
+        return goal_costmap_cost(p, y);
     default:
         return NAN;
     }

@@ -36,9 +36,9 @@ extern "C" {
 
 /* model / cost / integrator codes */
 enum { OR_DYN_CARTPOLE = 0, OR_DYN_QUADROTOR = 1, OR_DYN_BICYCLE_MLP = 2,
-       OR_DYN_DOUBLE_INTEGRATOR = 3, OR_DYN_LINEAR = 4 };
+       OR_DYN_DOUBLE_INTEGRATOR = 3, OR_DYN_LINEAR = 4, OR_DYN_DIFF_DRIVE = 5 };
 enum { OR_COST_QUADRATIC = 0, OR_COST_QUAD_OBSTACLES = 1,
-       OR_COST_COSTMAP_SPEED = 2, OR_COST_CIRCLE = 3 };
+       OR_COST_COSTMAP_SPEED = 2, OR_COST_CIRCLE = 3, OR_COST_GOAL_COSTMAP = 4 };
 enum { OR_EULER = 0, OR_RK4 = 1 };
 enum { OR_OK = 0, OR_ERR_INVALID_ARG = 1, OR_ERR_NUMERIC = 5 };
 

@@ -360,3 +360,55 @@ def test_circle_cost_by_hand(oracle_lib):
     assert oracle.running_cost(p, [0.5, 0, 0, 0], [0, 0]) == pytest.approx(1012.0)
     assert oracle.running_cost(p, [3.0, 0, 0, 0], [0, 0]) == pytest.approx(1012.0)
     assert oracle.terminal_cost(p, [3.0, 0, 0, 0]) == 0.0
+
+
+# --------------------------------------------------------------------------
+# differential drive + goal / angle / costmap cost (the paper's benchmark)
+# --------------------------------------------------------------------------
+def test_diff_drive_constant_command_closed_form(oracle_lib):
+    # Euler with constant (v, w): theta_t = theta0 + t a, a = dt w, and the
+    # positions sum a geometric series of rotations (Dirichlet kernel)
+    p = W.diff_drive(K=4, T=100)
+    T, dt = p["T"], p["dt"]
+    v, w = 0.4, 0.3
+    traj, _ = oracle.rollout(p, np.tile([v, w], (T, 1)))
+    a, th0 = dt * w, p["x0"][2]
+    ker = math.sin(T * a / 2) / math.sin(a / 2)
+    mid = th0 + (T - 1) * a / 2
+    want = [p["x0"][0] + dt * v * ker * math.cos(mid), p["x0"][1] + dt * v * ker * math.sin(mid),
+            th0 + T * a]
+    np.testing.assert_allclose(traj[-1], want, rtol=1e-12, atol=1e-12)
+
+
+def test_diff_drive_clamps_commands(oracle_lib):
+    p = W.diff_drive(K=4, T=30)
+    lim = p["dyn_params"]          # [v_min, v_max, w_min, w_max]
+    rng = np.random.default_rng(5)
+    for hi in (True, False):
+        over = np.tile([lim[1] + 3.0, lim[3] + 2.0] if hi else [lim[0] - 3.0, lim[2] - 2.0], (30, 1))
+        at = np.tile([lim[1], lim[3]] if hi else [lim[0], lim[2]], (30, 1))
+        np.testing.assert_array_equal(oracle.rollout(p, over)[0], oracle.rollout(p, at)[0])
+    inside = rng.uniform([lim[0], lim[2]], [lim[1], lim[3]], size=(30, 2))
+    t1 = oracle.rollout(p, inside)[0]
+    t2 = oracle.rollout(p, inside * 1.0000001)[0]
+    assert np.abs(t1 - t2).max() > 0      # inside the limits the command acts unchanged
+
+
+def test_goal_costmap_cost_by_hand(oracle_lib):
+    p = W.diff_drive(K=4, T=4)
+    C = p["cost_params"]
+    g = C[3:6]
+    M = p["map"]
+    # at a cell centre the map term is the texel (row i = y, column j = x)
+    i, j = 37, 81
+    xc, yc = C[6] + (j + 0.5) * C[8], C[7] + (i + 0.5) * C[8]
+    assert oracle.costmap_sample(p, xc, yc) == pytest.approx(M[i, j], abs=1e-12)
+    # at the goal position, heading off by 3 pi / 2 (wraps to -pi / 2)
+    y = [g[0], g[1], g[2] + 1.5 * math.pi]
+    want = C[1] * (math.pi / 2) ** 2 + C[2] * oracle.costmap_sample(p, g[0], g[1])
+    assert oracle.running_cost(p, y, [0, 0]) == pytest.approx(want, rel=1e-12)
+    # off the goal by (1, -2), heading exact: 5 * 5 + map
+    y = [g[0] + 1.0, g[1] - 2.0, g[2] - 4 * math.pi]
+    want = C[0] * 5.0 + C[2] * oracle.costmap_sample(p, y[0], y[1])
+    assert oracle.running_cost(p, y, [0.3, 0.1]) == pytest.approx(want, rel=1e-12)
+    assert oracle.terminal_cost(p, y) == pytest.approx(want, rel=1e-12)

@@ -33,11 +33,13 @@ DYN_QUADROTOR = 1
 DYN_BICYCLE_MLP = 2
 DYN_DOUBLE_INTEGRATOR = 3
 DYN_LINEAR = 4
+DYN_DIFF_DRIVE = 5
 
 COST_QUADRATIC = 0
 COST_QUAD_OBSTACLES = 1
 COST_COSTMAP_SPEED = 2
 COST_CIRCLE = 3
+COST_GOAL_COSTMAP = 4
 
 EULER = 0
 RK4 = 1
@@ -186,6 +188,37 @@ def bicycle_mlp(K=16384, T=100, seed=SEED_BASE + 2, lam=1.0, beta=1, dt=0.02,
         cost_params=[c_map, c_speed, v_des, MAP_ORIGIN, MAP_ORIGIN, MAP_CELL],
         map=cmap, K=K, T=T, dt=dt, lam=lam, sigma=[1.0, 0.5], beta=beta, seed=seed,
         x0=x0, u_nom=u_nom)
+
+
+# --------------------------------------------------------------------------
+# the paper's own benchmark: differential drive, goal + angle + costmap cost
+# (Sec. V, Table of algorithm parameters)
+# --------------------------------------------------------------------------
+DD_MAP_N = 110          # 11 m x 11 m at 0.1 m per cell
+DD_MAP_ORIGIN = -5.5
+DD_K_SWEEP = (128, 256, 512, 1024, 2048, 4096, 6144, 8192, 16384)
+
+
+def diff_drive(K=16384, T=100, seed=SEED_BASE + 5, lam=1.0, beta=1, dt=0.02,
+               v_lim=(-0.35, 0.5), w_lim=(-0.5, 0.5), c_goal=5.0, c_angle=5.0,
+               c_obs=20.0, sigma=0.2):
+    """Differential drive, state [x, y, theta], control [v, omega] clamped to
+    the limits.  Dynamics params: [v_min, v_max, w_min, w_max].  Cost params:
+    [c_goal, c_angle, c_obs, gx, gy, g_theta, x_min, y_min, cell]; a
+    110 x 110 smoothed-noise obstacle map in [0, 1] (the paper's map is not
+    published) is passed separately."""
+    rng = np.random.default_rng(seed)
+    x0 = np.array([-3.0, -3.0, math.pi / 4]) + rng.uniform(-0.2, 0.2, size=3)
+    goal = np.array([3.0, 3.0, math.pi / 4]) + rng.uniform(-0.2, 0.2, size=3)
+    cmap = draw_costmap(rng, n=DD_MAP_N, blur_cells=3.0, scale=1.0)
+    return _problem(
+        name=f"diff_drive_K{K}_T{T}", dyn_kind=DYN_DIFF_DRIVE, integrator=EULER,
+        nx=3, nu=2, dyn_params=[v_lim[0], v_lim[1], w_lim[0], w_lim[1]],
+        cost_kind=COST_GOAL_COSTMAP,
+        cost_params=[c_goal, c_angle, c_obs, goal[0], goal[1], goal[2],
+                     DD_MAP_ORIGIN, DD_MAP_ORIGIN, MAP_CELL],
+        map=cmap, K=K, T=T, dt=dt, lam=lam, sigma=[sigma, sigma], beta=beta, seed=seed,
+        x0=x0, u_nom=np.zeros((T, 2)))
 
 
 # --------------------------------------------------------------------------
