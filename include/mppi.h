@@ -81,13 +81,18 @@ typedef enum {
  *                     + b2) + b3 adds to [yaw', v', e1', e2'].
  *  DOUBLE_INTEGRATOR  nx=4 [x, y, vx, vy], nu=2 [ax, ay]; no params.
  *  LINEAR             xdot = A x + B u; params [A(nx x nx), B(nx x nu)];
- *                     (nx, nu) in {(2,1), (4,2), (6,3), (8,4)}. */
+ *                     (nx, nu) in {(2,1), (4,2), (6,3), (8,4)}.
+ *  DIFF_DRIVE         nx=3 [x, y, theta], nu=2 [v, omega] (the paper's
+ *                     benchmark, Sec. V); params [v_min, v_max, w_min, w_max]:
+ *                     the command is clamped to the limits, then
+ *                     x' = v cos theta, y' = v sin theta, theta' = omega; Euler. */
 typedef enum {
     MPPI_DYN_CARTPOLE = 0,
     MPPI_DYN_QUADROTOR = 1,
     MPPI_DYN_BICYCLE_MLP = 2,
     MPPI_DYN_DOUBLE_INTEGRATOR = 3,
-    MPPI_DYN_LINEAR = 4
+    MPPI_DYN_LINEAR = 4,
+    MPPI_DYN_DIFF_DRIVE = 5
 } mppi_dyn_kind;
 
 /* Costs (l = running cost on the post-step state y and sampled control v,
@@ -109,12 +114,18 @@ typedef enum {
  *                  (double integrator only; Eq. 25):
  *                  l = c_ring (1{r^2 <= r_in^2} + 1{r^2 >= r_out^2})
  *                  + c_v |v_des - |v|| + c_h |h_des - (x vy - y vx)|, phi = 0;
- *                  the two indicators are taken in FP32 like the crash test. */
+ *                  the two indicators are taken in FP32 like the crash test.
+ *  GOAL_COSTMAP    params [c_goal, c_angle, c_obs, gx, gy, g_theta, x_min,
+ *                  y_min, cell] plus a map_h x map_w map (DIFF_DRIVE only; the
+ *                  paper's benchmark cost, Sec. V): l = phi = c_goal |p - g|^2
+ *                  + c_angle wrap(theta - g_theta)^2 + c_obs M(x, y), wrap =
+ *                  IEEE remainder by 2 pi, M bilinear as for COSTMAP_SPEED. */
 typedef enum {
     MPPI_COST_QUADRATIC = 0,
     MPPI_COST_QUAD_OBSTACLES = 1,
     MPPI_COST_COSTMAP_SPEED = 2,
-    MPPI_COST_CIRCLE = 3
+    MPPI_COST_CIRCLE = 3,
+    MPPI_COST_GOAL_COSTMAP = 4
 } mppi_cost_kind;
 
 typedef enum { MPPI_EULER = 0, MPPI_RK4 = 1 } mppi_integrator;

@@ -32,6 +32,7 @@ int expected_dyn_params(int kind, int nx, int nu) {
     case MPPI_DYN_BICYCLE_MLP: return 1 + 64 * 6 + 64 + 64 * 64 + 64 + 4 * 64 + 4;
     case MPPI_DYN_DOUBLE_INTEGRATOR: return 0;
     case MPPI_DYN_LINEAR: return nx * nx + nx * nu;
+    case MPPI_DYN_DIFF_DRIVE: return 4;
     default: return -1;
     }
 }
@@ -42,6 +43,7 @@ bool fixed_dims(int kind, int &nx, int &nu) {
     case MPPI_DYN_QUADROTOR: nx = 13; nu = 4; return true;
     case MPPI_DYN_BICYCLE_MLP: nx = 7; nu = 2; return true;
     case MPPI_DYN_DOUBLE_INTEGRATOR: nx = 4; nu = 2; return true;
+    case MPPI_DYN_DIFF_DRIVE: nx = 3; nu = 2; return true;
     default: return false;
     }
 }
@@ -238,6 +240,13 @@ mppi_status validate_cost(const mppi_dynamics_desc &d, const mppi_cost_desc &cd,
             return msg = "COSTMAP_SPEED needs 6 params (cell > 0) and a map of at least 2x2",
                    MPPI_ERR_INVALID_ARG;
         return MPPI_OK;
+    case MPPI_COST_GOAL_COSTMAP:
+        if (d.kind != MPPI_DYN_DIFF_DRIVE)
+            return msg = "GOAL_COSTMAP cost needs DIFF_DRIVE dynamics", MPPI_ERR_UNSUPPORTED;
+        if (cd.n_params != 9 || !cd.map || cd.map_h < 2 || cd.map_w < 2 || !(cd.params[8] > 0.f))
+            return msg = "GOAL_COSTMAP needs 9 params (cell > 0) and a map of at least 2x2",
+                   MPPI_ERR_INVALID_ARG;
+        return MPPI_OK;
     case MPPI_COST_CIRCLE:
         if (d.kind != MPPI_DYN_DOUBLE_INTEGRATOR)
             return msg = "CIRCLE cost needs DOUBLE_INTEGRATOR dynamics", MPPI_ERR_UNSUPPORTED;
@@ -365,7 +374,7 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
         free_ctx(c);
         return e == cudaErrorMemoryAllocation ? MPPI_ERR_OOM : MPPI_ERR_CUDA;
     }
-    if (cost->kind == MPPI_COST_COSTMAP_SPEED) {
+    if (cost->kind == MPPI_COST_COSTMAP_SPEED || cost->kind == MPPI_COST_GOAL_COSTMAP) {
         c->map_h = cost->map_h;
         c->map_w = cost->map_w;
         const size_t n = static_cast<size_t>(cost->map_h) * cost->map_w;

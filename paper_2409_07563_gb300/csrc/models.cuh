@@ -195,6 +195,28 @@ struct DoubleIntegratorDyn {
     }
 };
 
+// Differential drive of the paper's benchmark (Sec. V, Table of algorithm
+// parameters): state [x, y, theta], control [v, omega], each clamped to its
+// limits P = [v_min, v_max, w_min, w_max] before it acts; Euler.
+struct DiffDriveDyn {
+    static constexpr int NX = 3, NU = 2;
+    static constexpr bool kPipelineNoise = true;
+    __host__ __device__ static int smem_floats(int) { return 4; }
+    __device__ static void prepare(const float *raw, float *s, int tid, int nt) {
+        for (int i = tid; i < 4; i += nt) s[i] = raw[i];
+    }
+    __device__ __forceinline__ static void step(float x[3], const float v[2], const float *P,
+                                                float dt) {
+        const float vc = fminf(fmaxf(v[0], P[0]), P[1]);
+        const float wc = fminf(fmaxf(v[1], P[2]), P[3]);
+        float sn, cs;
+        sincosf(x[2], &sn, &cs);
+        x[0] += dt * (vc * cs);
+        x[1] += dt * (vc * sn);
+        x[2] += dt * wc;
+    }
+};
+
 // Linear xdot = A x + B u: params [A (NX x NX), B (NX x NU)] row-major.
 template <int NX_, int NU_>
 struct LinearDyn {
@@ -309,6 +331,27 @@ struct QuadObstacleCost {
     }
 };
 
+// Bilinear costmap lookup between cell centres (x_min + (j + 1/2) cell,
+// y_min + (i + 1/2) cell), row i = y, clamped to the centre range; inv_cell =
+// 1 / cell.  Every index stays inside the map for any finite or infinite
+// (x, y), and for NaN (fmaxf returns the other operand).
+__device__ __forceinline__ float costmap_bilinear(float x, float y, float x_min, float y_min,
+                                                  float inv_cell, const CostCtx &cc) {
+    const int W = cc.map_w, H = cc.map_h;
+    float gx = (x - x_min) * inv_cell - 0.5f;
+    float gy = (y - y_min) * inv_cell - 0.5f;
+    gx = fminf(fmaxf(gx, 0.0f), static_cast<float>(W - 1));
+    gy = fminf(fmaxf(gy, 0.0f), static_cast<float>(H - 1));
+    const int j0 = min(static_cast<int>(floorf(gx)), W - 2);
+    const int i0 = min(static_cast<int>(floorf(gy)), H - 2);
+    const float fx = gx - static_cast<float>(j0), fy = gy - static_cast<float>(i0);
+    const float *m = cc.map + static_cast<size_t>(i0) * W + j0;
+    const float a = __ldg(m), b = __ldg(m + 1), c = __ldg(m + W), d = __ldg(m + W + 1);
+    const float top = a + fx * (b - a);
+    const float bot = c + fx * (d - c);
+    return top + fy * (bot - top);
+}
+
 // Costmap + speed tracking (bicycle): params [c_map, c_speed, v_des, x_min,
 // y_min, cell]; shared copy adds 1/cell at 6.
 struct CostmapSpeedCost {
@@ -319,24 +362,40 @@ struct CostmapSpeedCost {
     }
     __device__ __forceinline__ static float sample(float x, float y, const float *C,
                                                    const CostCtx &cc) {
-        const int W = cc.map_w, H = cc.map_h;
-        float gx = (x - C[3]) * C[6] - 0.5f;
-        float gy = (y - C[4]) * C[6] - 0.5f;
-        gx = fminf(fmaxf(gx, 0.0f), static_cast<float>(W - 1));
-        gy = fminf(fmaxf(gy, 0.0f), static_cast<float>(H - 1));
-        const int j0 = min(static_cast<int>(floorf(gx)), W - 2);
-        const int i0 = min(static_cast<int>(floorf(gy)), H - 2);
-        const float fx = gx - static_cast<float>(j0), fy = gy - static_cast<float>(i0);
-        const float *m = cc.map + static_cast<size_t>(i0) * W + j0;
-        const float a = __ldg(m), b = __ldg(m + 1), c = __ldg(m + W), d = __ldg(m + W + 1);
-        const float top = a + fx * (b - a);
-        const float bot = c + fx * (d - c);
-        return top + fy * (bot - top);
+        return costmap_bilinear(x, y, C[3], C[4], C[6], cc);
     }
     __device__ __forceinline__ static float state_cost(const float *y, const float *C,
                                                        const CostCtx &cc) {
         const float dv = y[3] - C[2];
         return C[0] * sample(y[0], y[1], C, cc) + C[1] * dv * dv;
+    }
+    __device__ __forceinline__ static float running(const float *y, const float *,
+                                                    const float *C, const CostCtx &cc) {
+        return state_cost(y, C, cc);
+    }
+    __device__ __forceinline__ static float terminal(const float *y, const float *C,
+                                                     const CostCtx &cc) {
+        return state_cost(y, C, cc);
+    }
+};
+
+// Goal position, goal angle and costmap obstacle cost of the paper's
+// benchmark (Sec. V, Table of algorithm parameters): params [c_goal, c_angle,
+// c_obs, gx, gy, g_theta, x_min, y_min, cell]; shared copy adds 1/cell at 9.
+// l = phi = c_goal |p - g|^2 + c_angle wrap(theta - g_theta)^2 + c_obs M(x, y),
+// wrap into [-pi, pi] by the IEEE remainder.
+struct GoalCostmapCost {
+    __host__ __device__ static int smem_floats(int) { return 12; }
+    __device__ static void prepare(const float *raw, float *s, int tid, int nt) {
+        for (int i = tid; i < 9; i += nt) s[i] = raw[i];
+        if (tid == 0) s[9] = 1.0f / raw[8];
+    }
+    __device__ __forceinline__ static float state_cost(const float *y, const float *C,
+                                                       const CostCtx &cc) {
+        const float dx = y[0] - C[3], dy = y[1] - C[4];
+        const float da = remainderf(y[2] - C[5], 6.28318530717958647692f);
+        return C[0] * (dx * dx + dy * dy) + C[1] * (da * da) +
+               C[2] * costmap_bilinear(y[0], y[1], C[6], C[7], C[9], cc);
     }
     __device__ __forceinline__ static float running(const float *y, const float *,
                                                     const float *C, const CostCtx &cc) {

@@ -92,6 +92,10 @@ bool dispatch(int dyn, int cost, int nx, int nu, F &&f) {
         if (cost == MPPI_COST_QUADRATIC)
             return f((DoubleIntegratorDyn *)0, (QuadraticCost<4, 2> *)0);
         return false;
+    case MPPI_DYN_DIFF_DRIVE:
+        if (cost == MPPI_COST_GOAL_COSTMAP) return f((DiffDriveDyn *)0, (GoalCostmapCost *)0);
+        if (cost == MPPI_COST_QUADRATIC) return f((DiffDriveDyn *)0, (QuadraticCost<3, 2> *)0);
+        return false;
     case MPPI_DYN_LINEAR:
         if (cost != MPPI_COST_QUADRATIC) return false;
         if (nx == 2 && nu == 1) return f((LinearDyn<2, 1> *)0, (QuadraticCost<2, 1> *)0);

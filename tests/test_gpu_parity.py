@@ -247,6 +247,24 @@ def test_bicycle_ragged(m, variant):
     compare(p, g)
 
 
+@pytest.mark.parametrize("K", [128, 1024, 16384])
+def test_diff_drive_benchmark(m, K):
+    """The paper's benchmark workload (differential drive, goal + angle +
+    costmap cost, T = 100, lambda = 1, sigma = 0.2) at sizes of its K sweep."""
+    p = as_f32_problem(W.diff_drive(K=K))
+    g, _ = run_gpu(m, p)
+    compare(p, g)
+
+
+@pytest.mark.parametrize("K,T", [(1000, 37), (129, 5), (33, 1)])
+def test_diff_drive_ragged(m, K, T):
+    # spread weights (lambda large) so the update averages many samples; the
+    # commands often hit their limits (sigma 0.6)
+    p = as_f32_problem(W.diff_drive(K=K, T=T, lam=2000.0, sigma=0.6))
+    g, _ = run_gpu(m, p)
+    compare(p, g)
+
+
 @pytest.mark.parametrize("cost", ["circle", "quadratic"])
 def test_double_integrator(m, cost):
     p = as_f32_problem(W.double_integrator(K=333, T=50, cost=cost, lam=50.0))
