@@ -45,6 +45,8 @@ UNIT = "rollout-steps/s"
 #    32 x 10, noise scaling + importance term 31, compensated accumulation 4.
 #  cart-pole: Euler step 30, quadratic cost 14, noise + importance term 7,
 #    compensated accumulation 4.
+#  diff drive (the paper's benchmark): dynamics 8, goal and angle terms 10,
+#    costmap bilinear 15, noise + importance 14, compensated accumulation 4.
 #  bicycle + MLP: MLP 2 (6*64 + 64*64 + 64*4) + 132 biases = 9604, kinematics
 #    and Euler 20, costmap bilinear + speed cost 15, noise + importance 14,
 #    compensated accumulation 4.
@@ -53,12 +55,14 @@ FLOPS_PER_ROLLOUT_STEP = {
     "quadrotor": QUAD_FLOPS_PER_ROLLOUT_STEP,
     "cartpole": 30 + 14 + 7 + 4,
     "bicycle": 9604 + 20 + 15 + 14 + 4,
+    "diffdrive": 8 + 10 + 15 + 14 + 4,
 }
 KERNEL_NAME = {
     "quadrotor": "quad_pair_kernel<true,false> (one sample per thread; dynamics, two noise and "
                  "a cost warp per 32 samples)",
     "cartpole": "rollout_kernel<CartpoleDyn, QuadraticCost<4,1>>",
     "bicycle": "bicycle_mlp_f32_kernel (four lanes per sample, FP32 CUDA cores)",
+    "diffdrive": "rollout_kernel<DiffDriveDyn, GoalCostmapCost>",
 }
 # FP32 pipe: 128 FP32 lanes per SM, 2 flops per FMA.
 FP32_LANES_PER_SM = 128
@@ -248,6 +252,8 @@ def make_workload(name, K=None):
         return W.cartpole(**kw)
     if name == "bicycle":
         return W.bicycle_mlp(**kw)
+    if name == "diffdrive":
+        return W.diff_drive(**kw)
     raise ValueError(name)
 
 
@@ -284,7 +290,8 @@ def time_steps_flushed(fn, steps, flush, warmup=3):
 
 
 def extensions(m, dev, peak_tflops, bf16_peak):
-    """The batched, differentiable, multi-iteration, CEM and BF16-MLP forms on the
+    """The batched, differentiable, multi-iteration, CEM and BF16-MLP forms, and
+    the paper's own diff-drive benchmark over its K sweep, on the
     same GPU, and the quadrotor on a K sweep (where the FP32 roofline fraction
     is the meaningful figure)."""
     import torch
@@ -373,6 +380,37 @@ def extensions(m, dev, peak_tflops, bf16_peak):
                   "rollout_steps_per_s": p["K"] * p["T"] / (ms_cem * 1e-3),
                   "elite_select_ms": prof["other"][0] / max(1, prof["other"][1])}
     ctl.close()
+    # the paper's own benchmark: differential drive, goal + angle + costmap
+    # cost, T = 100, over its K sweep; device-resident and end to end from
+    # host buffers (the paper's times include the host round trips).  The
+    # paper's RTX 4090 + i9-13900K times are context, not a target.
+    paper_4090_ms = {128: 0.1227, 256: 0.1219, 512: 0.1236, 1024: 0.1307, 2048: 0.1462,
+                     4096: 0.1700, 6144: 0.2006, 8192: 0.2316, 16384: 0.3886}
+    sweep = []
+    for K in W.DD_K_SWEEP:
+        p = W.diff_drive(K=K)
+        ctl = m.MPPI.from_problem(p)
+        x0 = torch.tensor(p["x0"], dtype=torch.float32, device=dev)
+        u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device=dev)
+        un = torch.empty_like(u)
+        ms_dev = time_steps_flushed(lambda: ctl.step_into(x0, u, un), 20, flush)
+        x0_h = torch.tensor(p["x0"], dtype=torch.float32).pin_memory()
+        u_h = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32).pin_memory()
+        un_h = torch.empty_like(u_h).pin_memory()
+        st_h = torch.empty(4, dtype=torch.float32).pin_memory()
+        for _ in range(3):
+            ctl.step_host_ptr(x0_h.data_ptr(), u_h.data_ptr(), un_h.data_ptr(), st_h.data_ptr())
+        t0 = time.perf_counter()
+        for _ in range(50):
+            ctl.step_host_ptr(x0_h.data_ptr(), u_h.data_ptr(), un_h.data_ptr(), st_h.data_ptr())
+        ms_e2e = (time.perf_counter() - t0) * 1e3 / 50
+        sweep.append({"K": K, "ms_per_step": ms_dev, "e2e_ms_per_step": ms_e2e,
+                      "rollout_steps_per_s": K * p["T"] / (ms_dev * 1e-3),
+                      "paper_rtx4090_ms": paper_4090_ms[K]})
+        ctl.close()
+    out["diffdrive_sweep"] = {"workload": "differential drive, goal + angle + costmap "
+                                          "(110 x 110), T=100, lambda=1, sigma=0.2",
+                              "points": sweep}
     # precision: bicycle + MLP, BF16 tensor cores vs FP32 CUDA cores
     p = W.bicycle_mlp()
     x0 = torch.tensor(p["x0"], dtype=torch.float32, device=dev)
