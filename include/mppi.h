@@ -118,8 +118,9 @@ typedef enum {
  *  GOAL_COSTMAP    params [c_goal, c_angle, c_obs, gx, gy, g_theta, x_min,
  *                  y_min, cell] plus a map_h x map_w map (DIFF_DRIVE only; the
  *                  paper's benchmark cost, Sec. V): l = phi = c_goal |p - g|^2
- *                  + c_angle wrap(theta - g_theta)^2 + c_obs M(x, y), wrap =
- *                  IEEE remainder by 2 pi, M bilinear as for COSTMAP_SPEED. */
+ *                  + c_angle wrap(theta - g_theta)^2 + c_obs M(x, y), wrap(d) =
+ *                  d - 2 pi rint(d / 2 pi) (the remainder by 2 pi), M bilinear
+ *                  as for COSTMAP_SPEED. */
 typedef enum {
     MPPI_COST_QUADRATIC = 0,
     MPPI_COST_QUAD_OBSTACLES = 1,

@@ -383,7 +383,8 @@ struct CostmapSpeedCost {
 // benchmark (Sec. V, Table of algorithm parameters): params [c_goal, c_angle,
 // c_obs, gx, gy, g_theta, x_min, y_min, cell]; shared copy adds 1/cell at 9.
 // l = phi = c_goal |p - g|^2 + c_angle wrap(theta - g_theta)^2 + c_obs M(x, y),
-// wrap into [-pi, pi] by the IEEE remainder.
+// wrap(d) = d - 2 pi rint(d / 2 pi) in [-pi, pi] (the IEEE remainder by 2 pi,
+// here without a branch: one rounding for the quotient, one fused multiply-add).
 struct GoalCostmapCost {
     __host__ __device__ static int smem_floats(int) { return 12; }
     __device__ static void prepare(const float *raw, float *s, int tid, int nt) {
@@ -393,7 +394,8 @@ struct GoalCostmapCost {
     __device__ __forceinline__ static float state_cost(const float *y, const float *C,
                                                        const CostCtx &cc) {
         const float dx = y[0] - C[3], dy = y[1] - C[4];
-        const float da = remainderf(y[2] - C[5], 6.28318530717958647692f);
+        const float d = y[2] - C[5];
+        const float da = fmaf(-6.28318530717958647692f, rintf(d * 0.159154943091895335769f), d);
         return C[0] * (dx * dx + dy * dy) + C[1] * (da * da) +
                C[2] * costmap_bilinear(y[0], y[1], C[6], C[7], C[9], cc);
     }

@@ -39,24 +39,30 @@ __device__ __forceinline__ float generic_sample_cost(const SampleArgs &a, uint32
     // the block drawn after the last group is never used
     float z[4 * NU];
     group_normals<NU>(a.nk, k, 0, QT, z);
+    auto one_step = [&](int t, int s) {
+        float v[NU];
+        float is = 0.f;
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+            const float u = a.s_u[t * NU + j];
+            v[j] = u + sig[j] * z[4 * j + s];
+            is += (v[j] - 0.5f * u) * (u * ivar[j]);
+        }
+        Dyn::step(x, v, a.s_dyn, a.dt);
+        J.add(Cost::running(x, v, a.s_cost, a.cc) + a.lam_beta * is);
+    };
     for (int t0 = 0; t0 < T; t0 += 4) {
         float zn[4 * NU];
         if (Dyn::kPipelineNoise) group_normals<NU>(a.nk, k, t0 + 4, QT, zn);
+        if (t0 + 4 <= T) {
+            // a whole group without per-step conditions, so the compiler can
+            // overlap one step's cost with the next step's dynamics
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const int t = t0 + s;
-            if (t < T) {
-                float v[NU];
-                float is = 0.f;
+            for (int s = 0; s < 4; ++s) one_step(t0 + s, s);
+        } else {
 #pragma unroll
-                for (int j = 0; j < NU; ++j) {
-                    const float u = a.s_u[t * NU + j];
-                    v[j] = u + sig[j] * z[4 * j + s];
-                    is += (v[j] - 0.5f * u) * (u * ivar[j]);
-                }
-                Dyn::step(x, v, a.s_dyn, a.dt);
-                J.add(Cost::running(x, v, a.s_cost, a.cc) + a.lam_beta * is);
-            }
+            for (int s = 0; s < 4; ++s)
+                if (t0 + s < T) one_step(t0 + s, s);
         }
         if (Dyn::kPipelineNoise) {
 #pragma unroll
