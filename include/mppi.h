@@ -166,9 +166,12 @@ typedef struct {
                                  thread with a dynamics warp, two noise warps and a
                                  cost warp per 32 samples (2-4: QUADROTOR with at most
                                  32 obstacles).  BICYCLE_MLP with COSTMAP_SPEED at
-                                 FP32: 0 takes four lanes per sample (the MLP's
-                                 hidden units split over the lanes), 1 one sample
-                                 per thread */
+                                 FP32: 0 takes four lanes per two samples (the
+                                 MLP's hidden units split over the lanes), 1 one
+                                 sample per thread.  The other models: 0 takes a
+                                 dynamics warp and a noise-and-cost warp per 32
+                                 samples (block_threads a multiple of 64, else one
+                                 sample per thread), 1 one sample per thread */
     int reserved[6];
 } mppi_options;
 

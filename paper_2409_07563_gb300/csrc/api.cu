@@ -115,14 +115,17 @@ void plan_launch(mppi_ctx &c) {
     const bool group = quad && !pair1 && !split;
     const bool mlp_tc = c.precision == MPPI_PREC_BF16_MLP;
     const bool mlp32 = mppi::mlp_f32_applicable(c) && c.variant_opt != mppi::kVariantGeneric;
+    const bool gpair = !mlp_tc && c.variant_opt == 0 && mppi::pair_rollout_applicable(c) &&
+                       c.block_threads % 64 == 0;
     pl.variant = mlp_tc  ? mppi::kVariantMlpBf16
                  : mlp32 ? mppi::kVariantMlpF32
+                 : gpair ? mppi::kVariantGenericPair
                  : pair1 ? mppi::kVariantQuadPair
                  : split ? mppi::kVariantQuadSplit
                  : group ? mppi::kVariantQuadGroup
                          : mppi::kVariantGeneric;
     // threads per sample (the FP32 MLP: four lanes per two samples)
-    const int lanes = mlp_tc ? 2 : mlp32 ? 2 : split ? 8 : pair1 ? roles : group ? 4 : 1;
+    const int lanes = mlp_tc || mlp32 || gpair ? 2 : split ? 8 : pair1 ? roles : group ? 4 : 1;
     const long threads_needed = static_cast<long>(c.K) * lanes;
     if (c.block_threads > 0) {
         pl.rollout_threads = c.block_threads;
@@ -132,6 +135,12 @@ void plan_launch(mppi_ctx &c) {
         // pairs put one dynamics warp on each SM sub-partition (measured on
         // GB300 at K = 16384, T = 100: 122 us per step against 166 for one
         // pair per block, whose dynamics warps share two sub-partitions)
+        const long groups = (static_cast<long>(c.K) + 31) / 32;
+        const long per_sm = (groups + c.num_sms - 1) / c.num_sms;
+        pl.rollout_threads = 64 * static_cast<int>(std::min(4L, std::max(1L, per_sm)));
+    } else if (gpair) {
+        // warp pairs spread over every SM first, at most four per block (one
+        // dynamics warp per SM sub-partition; K = 1024: 32 blocks of one pair)
         const long groups = (static_cast<long>(c.K) + 31) / 32;
         const long per_sm = (groups + c.num_sms - 1) / c.num_sms;
         pl.rollout_threads = 64 * static_cast<int>(std::min(4L, std::max(1L, per_sm)));
@@ -403,6 +412,7 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
         : c->plan.variant == mppi::kVariantQuadPair ? mppi::quad_pair_smem_bytes(*c, c->plan.rollout_threads)
         : c->plan.variant == mppi::kVariantMlpBf16 ? mppi::mlp_bf16_smem_bytes(*c, c->plan.rollout_threads)
         : c->plan.variant == mppi::kVariantMlpF32 ? mppi::mlp_f32_smem_bytes(*c, c->plan.rollout_threads)
+        : c->plan.variant == mppi::kVariantGenericPair ? mppi::pair_rollout_smem_bytes(*c, c->plan.rollout_threads)
                                                    : mppi::rollout_smem_bytes(*c);
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
@@ -415,7 +425,8 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
         (c->plan.variant == mppi::kVariantQuadSplit && (e = mppi::quad_split_prepare(*c)) != cudaSuccess) ||
         (c->plan.variant == mppi::kVariantQuadPair && (e = mppi::quad_pair_prepare(*c)) != cudaSuccess) ||
         (c->plan.variant == mppi::kVariantMlpBf16 && (e = mppi::mlp_bf16_prepare(*c)) != cudaSuccess) ||
-        (c->plan.variant == mppi::kVariantMlpF32 && (e = mppi::mlp_f32_prepare(*c)) != cudaSuccess)) {
+        (c->plan.variant == mppi::kVariantMlpF32 && (e = mppi::mlp_f32_prepare(*c)) != cudaSuccess) ||
+        (c->plan.variant == mppi::kVariantGenericPair && (e = mppi::pair_rollout_prepare(*c)) != cudaSuccess)) {
         free_ctx(c);
         return MPPI_ERR_CUDA;
     }
@@ -461,6 +472,7 @@ mppi_status mppi_step(mppi_ctx *ctx, const float *x0_d, const float *u_nom_d, fl
                 : ctx->plan.variant == mppi::kVariantQuadPair ? mppi::launch_quad_pair(*ctx, p)
                 : ctx->plan.variant == mppi::kVariantMlpBf16 ? mppi::launch_mlp_bf16(*ctx, p)
                 : ctx->plan.variant == mppi::kVariantMlpF32 ? mppi::launch_mlp_f32(*ctx, p)
+                : ctx->plan.variant == mppi::kVariantGenericPair ? mppi::launch_pair_rollout(*ctx, p)
                                                              : mppi::launch_rollout(*ctx, p);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "rollout launch");

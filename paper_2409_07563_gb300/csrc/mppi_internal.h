@@ -71,7 +71,8 @@ enum RolloutVariant {
     kVariantQuadSplit = 3,
     kVariantQuadPair = 4,
     kVariantMlpBf16 = 5,
-    kVariantMlpF32 = 6
+    kVariantMlpF32 = 6,
+    kVariantGenericPair = 7
 };
 
 struct LaunchPlan {
@@ -124,6 +125,11 @@ bool rollout_supported(int dyn_kind, int cost_kind, int nx, int nu);
 size_t rollout_smem_bytes(const mppi_ctx &c);
 cudaError_t rollout_prepare(const mppi_ctx &c);  // sets smem attributes
 cudaError_t launch_rollout(const mppi_ctx &c, const StepParams &p);
+// the same models with a dynamics warp and a noise-and-cost warp per 32 samples
+bool pair_rollout_applicable(const mppi_ctx &c);
+size_t pair_rollout_smem_bytes(const mppi_ctx &c, int threads);
+cudaError_t pair_rollout_prepare(const mppi_ctx &c);
+cudaError_t launch_pair_rollout(const mppi_ctx &c, const StepParams &p);
 cudaError_t launch_update(const mppi_ctx &c, const StepParams &p);
 // the state trajectory of x0 under u (no noise): traj[(T+1) nx]
 cudaError_t launch_nominal_trajectory(const mppi_ctx &c, const float *x0, const float *u,

@@ -1,7 +1,8 @@
-// rollout.cu -- fused noise + rollout + cost kernel (steps a1-a3) with the
-// weight-statistics reduction (step a4) folded into its tail.
+// rollout.cu -- fused noise + rollout + cost kernels (steps a1-a3) with the
+// weight-statistics reduction (step a4) folded into their tail, for every
+// model; the output trajectory and the MPC shift.
 //
-// One sample per thread.  For every group of 4 time steps the thread draws
+// rollout_kernel, one sample per thread.  For every group of 4 time steps the thread draws
 // one Philox block per control channel (4*NU normals, Sec. II-C sampling of
 // eps; drawn one group ahead), then runs x <- F(x, u + eps),
 // J += l(x, v) - lambda I(v) (Algorithm 1 inner loop) with state and cost in
@@ -10,6 +11,11 @@
 // (rho_b, eta_b, eta2_b) relative to its own minimum; the last block to finish
 // (atomic ticket, no waiting) merges the partials with a log-sum-exp rescale
 // into rho, eta, F and ESS (Eq. 17-18 and Eq. 4).
+// pair_rollout_kernel (the default for the models without a kernel of their
+// own): the same arithmetic split between a dynamics warp and a
+// noise-and-cost warp per 32 samples (see below).
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "models.cuh"
 #include "mppi_internal.h"
@@ -62,6 +68,162 @@ __global__ void __launch_bounds__(256) rollout_kernel(const StepParams p) {
     }
 
     block_weight_tail(p, S, k < p.K ? k : -1, s_red, blockDim.x, s_u);
+}
+
+// ---------------------------------------------------------------------------
+// Warp pairs: per 32 samples (one per lane) a dynamics warp and a
+// noise-and-cost warp.  The dynamics warp only steps the model, reading v_t
+// from a shared ring and leaving x_{t+1} there; the partner draws the noise
+// for the next four steps (one Philox block per channel), and scores the
+// states of the previous four (running cost with the importance term,
+// recomputed from the ring's v_t exactly as the one-thread kernel computes
+// it, in the same order, then the terminal cost).  The ring holds two halves
+// of kPairSteps steps, [half][step][component][lane]; the warps meet at one
+// named barrier per half (id 1 + pair, 64 threads) and both execute 1 + nh
+// barriers (the loops depend on T only).  Samples beyond K are computed and
+// discarded.
+// ---------------------------------------------------------------------------
+constexpr int kPairSteps = 4;
+
+template <class Dyn>
+__host__ __device__ constexpr int pair_ring_floats() {
+    return 2 * kPairSteps * (Dyn::NX + Dyn::NU) * kWarp;
+}
+
+__device__ __forceinline__ void pair_sync(int id) {
+    asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
+template <class Dyn, class Cost>
+__global__ void __launch_bounds__(256) pair_rollout_kernel(const StepParams p) {
+    constexpr int NX = Dyn::NX, NU = Dyn::NU, H = kPairSteps;
+    extern __shared__ __align__(16) float smem[];
+    const Layout<Dyn, Cost> L(p.T, p.n_dyn_params, p.n_cost_params);
+    float *s_u = smem + L.u;
+    float *s_dyn = smem + L.dyn;
+    float *s_cost = smem + L.cost;
+    float *s_red = smem + L.red;
+    const int tid = threadIdx.x, nt = blockDim.x, T = p.T;
+    const int G = nt / (2 * kWarp);
+    const int warp = tid / kWarp, lane = tid % kWarp;
+    const int role = warp / G, pair = warp % G;
+    float *ring_v = smem + L.total + pair * pair_ring_floats<Dyn>();  // [2][H][NU][32]
+    float *ring_x = ring_v + 2 * H * NU * kWarp;                      // [2][H][NX][32]
+    wait_for_predecessor();
+    for (int i = tid; i < T * NU; i += nt) s_u[i] = p.u_nom[i];
+    Dyn::prepare(p.dyn_params, s_dyn, tid, nt);
+    Cost::prepare(p.cost_params, s_cost, tid, nt);
+    __syncthreads();
+    if (p.saved_in && blockIdx.x == 0) {  // inputs kept for a later backward
+        for (int i = tid; i < NX; i += nt) p.saved_in[i] = p.x0[i];
+        for (int i = tid; i < T * NU; i += nt) p.saved_in[NX + i] = s_u[i];
+    }
+    const int k = (blockIdx.x * G + pair) * kWarp + lane;
+    const int nh = (T + H - 1) / H;
+    const int bar_id = 1 + pair;
+    float S = __int_as_float(0x7f800000);
+    int k_out = -1;
+    if (role == 0) {
+        float x[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) x[i] = p.x0[i];
+        pair_sync(bar_id);  // the controls of half 0 are in the ring
+        for (int hh = 0; hh < nh; ++hh) {
+            const float *vb = ring_v + (hh & 1) * H * NU * kWarp;
+            float *xb = ring_x + (hh & 1) * H * NX * kWarp;
+            const int ns = min(H, T - hh * H);
+            auto one = [&](int s) {
+                float v[NU];
+#pragma unroll
+                for (int j = 0; j < NU; ++j) v[j] = vb[(s * NU + j) * kWarp + lane];
+                Dyn::step(x, v, s_dyn, p.dt);
+#pragma unroll
+                for (int i = 0; i < NX; ++i) xb[(s * NX + i) * kWarp + lane] = x[i];
+            };
+            if (ns == H) {
+#pragma unroll
+                for (int s = 0; s < H; ++s) one(s);
+            } else {
+                for (int s = 0; s < ns; ++s) one(s);
+            }
+            pair_sync(bar_id);
+        }
+    } else {
+        const NoiseKey nk = make_noise_key(p.seed, *p.counter);
+        const CostCtx cc{p.map, p.map_h, p.map_w};
+        const int QT = (T + 3) / 4;
+        float sig[NU], ivar[NU];
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+            sig[j] = p.sigma[j];
+            ivar[j] = p.ivar[j];
+        }
+        CompSum J;
+        float x_last[NX];
+        // v_t = u_t + sigma z_t for the steps of half hc (one Philox block per
+        // channel: a half is one noise group)
+        auto controls = [&](int hc) {
+            float *vb = ring_v + (hc & 1) * H * NU * kWarp;
+            float z[4 * NU];
+            group_normals<NU>(nk, static_cast<uint32_t>(k), hc * H, QT, z);
+            const int nc = min(H, T - hc * H);
+#pragma unroll
+            for (int s = 0; s < H; ++s)
+                if (s < nc)
+#pragma unroll
+                    for (int j = 0; j < NU; ++j)
+                        vb[(s * NU + j) * kWarp + lane] =
+                            s_u[(hc * H + s) * NU + j] + sig[j] * z[4 * j + s];
+        };
+        // running cost of x_{t+1} with the importance term of v_t
+        auto cost_of = [&](int hs, int s) {
+            const float *vb = ring_v + (hs & 1) * H * NU * kWarp;
+            const float *xb = ring_x + (hs & 1) * H * NX * kWarp;
+            const int t = hs * H + s;
+            float v[NU], y[NX];
+            float is = 0.f;
+#pragma unroll
+            for (int j = 0; j < NU; ++j) {
+                const float u = s_u[t * NU + j];
+                v[j] = vb[(s * NU + j) * kWarp + lane];
+                is += (v[j] - 0.5f * u) * (u * ivar[j]);
+            }
+#pragma unroll
+            for (int i = 0; i < NX; ++i) y[i] = xb[(s * NX + i) * kWarp + lane];
+            if (t == T - 1)
+#pragma unroll
+                for (int i = 0; i < NX; ++i) x_last[i] = y[i];
+            return Cost::running(y, v, s_cost, cc) + p.lam_beta * is;
+        };
+        auto states = [&](int hs) {
+            const int ns = min(H, T - hs * H);
+            if (ns == H) {  // the half's costs are independent: evaluate, then add in order
+                float c[H];
+#pragma unroll
+                for (int s = 0; s < H; ++s) c[s] = cost_of(hs, s);
+#pragma unroll
+                for (int s = 0; s < H; ++s) J.add(c[s]);
+            } else {
+                for (int s = 0; s < ns; ++s) J.add(cost_of(hs, s));
+            }
+        };
+        controls(0);
+        pair_sync(bar_id);
+        for (int hh = 0; hh < nh; ++hh) {
+            // half hh - 1 is read before half hh + 1 overwrites its ring slot
+            if (hh >= 1) states(hh - 1);
+            if (hh + 1 < nh) controls(hh + 1);
+            pair_sync(bar_id);
+        }
+        states(nh - 1);
+        J.add(Cost::terminal(x_last, s_cost, cc));
+        if (k < p.K) {
+            S = J.value();
+            k_out = k;
+            p.S[k] = S;
+        }
+    }
+    block_weight_tail(p, S, k_out, s_red, kWarp * G, s_u);
 }
 
 template <class Dyn, class Cost>
@@ -191,6 +353,69 @@ cudaError_t rollout_prepare(const mppi_ctx &c) {
                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    static_cast<int>(smem_bytes_for<D, C>(c)));
         return true;
+    });
+    return err;
+}
+
+// models the warp-pair kernel is instantiated for (the quadrotor and the
+// bicycle + MLP have kernels of their own)
+template <class D>
+constexpr bool kPairModel = !std::is_same_v<D, QuadrotorDyn> && !std::is_same_v<D, BicycleMlpDyn>;
+
+bool pair_rollout_applicable(const mppi_ctx &c) {
+    // the quadrotor and the bicycle + MLP have kernels of their own
+    return c.dyn_kind != MPPI_DYN_QUADROTOR && c.dyn_kind != MPPI_DYN_BICYCLE_MLP &&
+           rollout_supported(c.dyn_kind, c.cost_kind, c.nx, c.nu);
+}
+
+size_t pair_rollout_smem_bytes(const mppi_ctx &c, int threads) {
+    size_t bytes = 0;
+    dispatch(c.dyn_kind, c.cost_kind, c.nx, c.nu, [&](auto *d, auto *cst) {
+        using D = std::remove_pointer_t<decltype(d)>;
+        using C = std::remove_pointer_t<decltype(cst)>;
+        if constexpr (!kPairModel<D>) {
+            return false;
+        } else {
+            bytes = smem_bytes_for<D, C>(c) + sizeof(float) * static_cast<size_t>(threads / 64) *
+                                                  pair_ring_floats<D>();
+            return true;
+        }
+    });
+    return bytes;
+}
+
+cudaError_t pair_rollout_prepare(const mppi_ctx &c) {
+    cudaError_t err = cudaSuccess;
+    dispatch(c.dyn_kind, c.cost_kind, c.nx, c.nu, [&](auto *d, auto *cst) {
+        using D = std::remove_pointer_t<decltype(d)>;
+        using C = std::remove_pointer_t<decltype(cst)>;
+        if constexpr (!kPairModel<D>) {
+            return false;
+        } else {
+            err = cudaFuncSetAttribute(pair_rollout_kernel<D, C>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(pair_rollout_smem_bytes(c, 256)));
+            return true;
+        }
+    });
+    return err;
+}
+
+cudaError_t launch_pair_rollout(const mppi_ctx &c, const StepParams &p) {
+    cudaError_t err = cudaErrorInvalidValue;
+    dispatch(c.dyn_kind, c.cost_kind, c.nx, c.nu, [&](auto *d, auto *cst) {
+        using D = std::remove_pointer_t<decltype(d)>;
+        using C = std::remove_pointer_t<decltype(cst)>;
+        if constexpr (!kPairModel<D>) {
+            return false;
+        } else {
+            cudaLaunchAttribute attr[1];
+            const cudaLaunchConfig_t cfg = pdl_config(dim3(c.plan.rollout_blocks),
+                                                      dim3(c.plan.rollout_threads),
+                                                      c.plan.rollout_smem, c.stream, attr);
+            err = cudaLaunchKernelEx(&cfg, pair_rollout_kernel<D, C>, p);
+            return true;
+        }
     });
     return err;
 }

@@ -225,10 +225,11 @@ def test_bicycle_four_lanes_block_sizes(m, bt, K, T):
 # --------------------------------------------------------------------------
 # test models, ragged sizes (several blocks plus a partial one)
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("K,T", [(1000, 37), (257, 5), (33, 101)])
-def test_cartpole_ragged(m, K, T):
+def test_cartpole_ragged(m, K, T, variant):
     p = as_f32_problem(W.cartpole(K=K, T=T, lam=20.0))
-    g, _ = run_gpu(m, p)
+    g, _ = run_gpu(m, p, rollout_variant=variant)
     compare(p, g)
 
 
@@ -247,12 +248,13 @@ def test_bicycle_ragged(m, variant):
     compare(p, g)
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("K", [128, 1024, 16384])
-def test_diff_drive_benchmark(m, K):
+def test_diff_drive_benchmark(m, K, variant):
     """The paper's benchmark workload (differential drive, goal + angle +
     costmap cost, T = 100, lambda = 1, sigma = 0.2) at sizes of its K sweep."""
     p = as_f32_problem(W.diff_drive(K=K))
-    g, _ = run_gpu(m, p)
+    g, _ = run_gpu(m, p, rollout_variant=variant)
     compare(p, g)
 
 
@@ -263,6 +265,37 @@ def test_diff_drive_ragged(m, K, T):
     p = as_f32_problem(W.diff_drive(K=K, T=T, lam=2000.0, sigma=0.6))
     g, _ = run_gpu(m, p)
     compare(p, g)
+
+
+PAIR_MODELS = [
+    ("cartpole", lambda K, T: W.cartpole(K=K, T=T, lam=20.0)),
+    ("diff_drive", lambda K, T: W.diff_drive(K=K, T=T, lam=2000.0, sigma=0.6)),
+    ("double_integrator", lambda K, T: W.double_integrator(K=K, T=T, lam=50.0)),
+    ("linear6x3", lambda K, T: W.linear(K=K, T=T, nx=6, nu=3, lam=20.0)),
+]
+
+
+@pytest.mark.parametrize("bt", [64, 128, 192, 256])
+@pytest.mark.parametrize("name,make", PAIR_MODELS, ids=[c[0] for c in PAIR_MODELS])
+@pytest.mark.parametrize("K,T", [(1000, 37), (33, 1), (97, 8), (300, 9)])
+def test_warp_pairs_block_sizes(m, bt, name, make, K, T):
+    """A dynamics warp and a noise-and-cost warp per 32 samples at every
+    block size, with ragged K and horizons that end inside a ring half, on
+    its edge, or within the first half."""
+    p = as_f32_problem(make(K, T))
+    g, _ = run_gpu(m, p, block_threads=bt)
+    compare(p, g)
+
+
+def test_warp_pairs_equal_one_thread_costs(m):
+    """The pair kernel does the one-thread kernel's arithmetic in the same
+    order: the costs agree to the last bit or nearly (compiler contraction
+    may differ), far inside the oracle bar."""
+    p = as_f32_problem(W.cartpole(K=1024, T=100))
+    a, _ = run_gpu(m, p, rollout_variant=0)
+    b, _ = run_gpu(m, p, rollout_variant=1)
+    rel = np.abs(a["costs"] - b["costs"]) / np.maximum(1.0, np.abs(b["costs"]))
+    assert rel.max() <= 1e-6
 
 
 @pytest.mark.parametrize("cost", ["circle", "quadratic"])
