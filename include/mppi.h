@@ -169,9 +169,9 @@ typedef struct {
                                  FP32: 0 takes four lanes per two samples (the
                                  MLP's hidden units split over the lanes), 1 one
                                  sample per thread.  The other models: 0 takes a
-                                 dynamics warp and a noise-and-cost warp per 32
-                                 samples (block_threads a multiple of 64, else one
-                                 sample per thread), 1 one sample per thread */
+                                 dynamics warp, a noise warp and a cost warp per 32
+                                 samples (block_threads 96 or 192, else one sample
+                                 per thread), 1 one sample per thread */
     int reserved[6];
 } mppi_options;
 

@@ -116,7 +116,7 @@ void plan_launch(mppi_ctx &c) {
     const bool mlp_tc = c.precision == MPPI_PREC_BF16_MLP;
     const bool mlp32 = mppi::mlp_f32_applicable(c) && c.variant_opt != mppi::kVariantGeneric;
     const bool gpair = !mlp_tc && c.variant_opt == 0 && mppi::pair_rollout_applicable(c) &&
-                       c.block_threads % 64 == 0;
+                       c.block_threads % 96 == 0 && c.block_threads <= 192;
     pl.variant = mlp_tc  ? mppi::kVariantMlpBf16
                  : mlp32 ? mppi::kVariantMlpF32
                  : gpair ? mppi::kVariantGenericPair
@@ -125,7 +125,7 @@ void plan_launch(mppi_ctx &c) {
                  : group ? mppi::kVariantQuadGroup
                          : mppi::kVariantGeneric;
     // threads per sample (the FP32 MLP: four lanes per two samples)
-    const int lanes = mlp_tc || mlp32 || gpair ? 2 : split ? 8 : pair1 ? roles : group ? 4 : 1;
+    const int lanes = mlp_tc || mlp32 ? 2 : gpair ? 3 : split ? 8 : pair1 ? roles : group ? 4 : 1;
     const long threads_needed = static_cast<long>(c.K) * lanes;
     if (c.block_threads > 0) {
         pl.rollout_threads = c.block_threads;
@@ -139,11 +139,12 @@ void plan_launch(mppi_ctx &c) {
         const long per_sm = (groups + c.num_sms - 1) / c.num_sms;
         pl.rollout_threads = 64 * static_cast<int>(std::min(4L, std::max(1L, per_sm)));
     } else if (gpair) {
-        // warp pairs spread over every SM first, at most four per block (one
-        // dynamics warp per SM sub-partition; K = 1024: 32 blocks of one pair)
+        // warp triples spread over every SM first, at most two per block (two
+        // blocks on an SM put their four dynamics warps on four sub-partitions;
+        // K = 1024: 32 blocks of one triple)
         const long groups = (static_cast<long>(c.K) + 31) / 32;
         const long per_sm = (groups + c.num_sms - 1) / c.num_sms;
-        pl.rollout_threads = 64 * static_cast<int>(std::min(4L, std::max(1L, per_sm)));
+        pl.rollout_threads = 96 * static_cast<int>(std::min(2L, std::max(1L, per_sm)));
     } else if (mlp32) {
         // sixteen samples per warp; two warps per block once there are two
         // warps per SM (K = 16384: 512 blocks, about seven warps per SM)

@@ -12,8 +12,8 @@
 // (atomic ticket, no waiting) merges the partials with a log-sum-exp rescale
 // into rho, eta, F and ESS (Eq. 17-18 and Eq. 4).
 // pair_rollout_kernel (the default for the models without a kernel of their
-// own): the same arithmetic split between a dynamics warp and a
-// noise-and-cost warp per 32 samples (see below).
+// own): the same arithmetic split between a dynamics warp, a noise warp and
+// a cost warp per 32 samples (see below).
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -71,32 +71,36 @@ __global__ void __launch_bounds__(256) rollout_kernel(const StepParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// Warp pairs: per 32 samples (one per lane) a dynamics warp and a
-// noise-and-cost warp.  The dynamics warp only steps the model, reading v_t
-// from a shared ring and leaving x_{t+1} there; the partner draws the noise
-// for the next four steps (one Philox block per channel), and scores the
-// states of the previous four (running cost with the importance term,
-// recomputed from the ring's v_t exactly as the one-thread kernel computes
-// it, in the same order, then the terminal cost).  The ring holds two halves
-// of kPairSteps steps, [half][step][component][lane]; the warps meet at one
-// named barrier per half (id 1 + pair, 64 threads) and both execute 1 + nh
+// Warp triples: per 32 samples (one per lane) a dynamics warp, a noise warp
+// and a cost warp.  The dynamics warp only steps the model, reading v_t from
+// a shared ring and leaving x_{t+1} there; the noise warp draws the controls
+// of the next four steps (one Philox block per channel: v = u + sigma z);
+// the cost warp scores the states of the previous four (running cost with
+// the importance term, recomputed from the ring's v_t exactly as the
+// one-thread kernel computes it, in the same order, then the terminal cost).
+// Rings per group, [slot][step][component][lane]: three slots of controls
+// (the noise warp fills half h + 1 while the dynamics warp reads half h and
+// the cost warp half h - 1) and two of states.  The warps meet at one named
+// barrier per half (id 1 + group, 96 threads) and all execute 1 + nh
 // barriers (the loops depend on T only).  Samples beyond K are computed and
 // discarded.
 // ---------------------------------------------------------------------------
 constexpr int kPairSteps = 4;
+constexpr int kPairRoles = 3;
 
 template <class Dyn>
 __host__ __device__ constexpr int pair_ring_floats() {
-    return 2 * kPairSteps * (Dyn::NX + Dyn::NU) * kWarp;
+    return kPairSteps * (3 * Dyn::NU + 2 * Dyn::NX) * kWarp;
 }
 
 __device__ __forceinline__ void pair_sync(int id) {
-    asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+    asm volatile("bar.sync %0, 96;" ::"r"(id) : "memory");
 }
 
 template <class Dyn, class Cost>
 __global__ void __launch_bounds__(256) pair_rollout_kernel(const StepParams p) {
     constexpr int NX = Dyn::NX, NU = Dyn::NU, H = kPairSteps;
+    constexpr int kVSlot = H * NU * kWarp, kXSlot = H * NX * kWarp;
     extern __shared__ __align__(16) float smem[];
     const Layout<Dyn, Cost> L(p.T, p.n_dyn_params, p.n_cost_params);
     float *s_u = smem + L.u;
@@ -104,11 +108,11 @@ __global__ void __launch_bounds__(256) pair_rollout_kernel(const StepParams p) {
     float *s_cost = smem + L.cost;
     float *s_red = smem + L.red;
     const int tid = threadIdx.x, nt = blockDim.x, T = p.T;
-    const int G = nt / (2 * kWarp);
+    const int G = nt / (kPairRoles * kWarp);
     const int warp = tid / kWarp, lane = tid % kWarp;
-    const int role = warp / G, pair = warp % G;
-    float *ring_v = smem + L.total + pair * pair_ring_floats<Dyn>();  // [2][H][NU][32]
-    float *ring_x = ring_v + 2 * H * NU * kWarp;                      // [2][H][NX][32]
+    const int role = warp / G, group = warp % G;
+    float *ring_v = smem + L.total + group * pair_ring_floats<Dyn>();  // [3][H][NU][32]
+    float *ring_x = ring_v + 3 * kVSlot;                                // [2][H][NX][32]
     wait_for_predecessor();
     for (int i = tid; i < T * NU; i += nt) s_u[i] = p.u_nom[i];
     Dyn::prepare(p.dyn_params, s_dyn, tid, nt);
@@ -118,9 +122,9 @@ __global__ void __launch_bounds__(256) pair_rollout_kernel(const StepParams p) {
         for (int i = tid; i < NX; i += nt) p.saved_in[i] = p.x0[i];
         for (int i = tid; i < T * NU; i += nt) p.saved_in[NX + i] = s_u[i];
     }
-    const int k = (blockIdx.x * G + pair) * kWarp + lane;
+    const int k = (blockIdx.x * G + group) * kWarp + lane;
     const int nh = (T + H - 1) / H;
-    const int bar_id = 1 + pair;
+    const int bar_id = 1 + group;
     float S = __int_as_float(0x7f800000);
     int k_out = -1;
     if (role == 0) {
@@ -129,8 +133,8 @@ __global__ void __launch_bounds__(256) pair_rollout_kernel(const StepParams p) {
         for (int i = 0; i < NX; ++i) x[i] = p.x0[i];
         pair_sync(bar_id);  // the controls of half 0 are in the ring
         for (int hh = 0; hh < nh; ++hh) {
-            const float *vb = ring_v + (hh & 1) * H * NU * kWarp;
-            float *xb = ring_x + (hh & 1) * H * NX * kWarp;
+            const float *vb = ring_v + (hh % 3) * kVSlot;
+            float *xb = ring_x + (hh & 1) * kXSlot;
             const int ns = min(H, T - hh * H);
             auto one = [&](int s) {
                 float v[NU];
@@ -148,22 +152,16 @@ __global__ void __launch_bounds__(256) pair_rollout_kernel(const StepParams p) {
             }
             pair_sync(bar_id);
         }
-    } else {
+    } else if (role == 1) {
         const NoiseKey nk = make_noise_key(p.seed, *p.counter);
-        const CostCtx cc{p.map, p.map_h, p.map_w};
         const int QT = (T + 3) / 4;
-        float sig[NU], ivar[NU];
+        float sig[NU];
 #pragma unroll
-        for (int j = 0; j < NU; ++j) {
-            sig[j] = p.sigma[j];
-            ivar[j] = p.ivar[j];
-        }
-        CompSum J;
-        float x_last[NX];
-        // v_t = u_t + sigma z_t for the steps of half hc (one Philox block per
-        // channel: a half is one noise group)
+        for (int j = 0; j < NU; ++j) sig[j] = p.sigma[j];
+        // v_t = u_t + sigma z_t for the steps of half hc (a half is one
+        // Philox group: one block per channel)
         auto controls = [&](int hc) {
-            float *vb = ring_v + (hc & 1) * H * NU * kWarp;
+            float *vb = ring_v + (hc % 3) * kVSlot;
             float z[4 * NU];
             group_normals<NU>(nk, static_cast<uint32_t>(k), hc * H, QT, z);
             const int nc = min(H, T - hc * H);
@@ -175,10 +173,23 @@ __global__ void __launch_bounds__(256) pair_rollout_kernel(const StepParams p) {
                         vb[(s * NU + j) * kWarp + lane] =
                             s_u[(hc * H + s) * NU + j] + sig[j] * z[4 * j + s];
         };
+        controls(0);
+        pair_sync(bar_id);
+        for (int hh = 0; hh < nh; ++hh) {
+            if (hh + 1 < nh) controls(hh + 1);
+            pair_sync(bar_id);
+        }
+    } else {
+        const CostCtx cc{p.map, p.map_h, p.map_w};
+        float ivar[NU];
+#pragma unroll
+        for (int j = 0; j < NU; ++j) ivar[j] = p.ivar[j];
+        CompSum J;
+        float x_last[NX];
         // running cost of x_{t+1} with the importance term of v_t
         auto cost_of = [&](int hs, int s) {
-            const float *vb = ring_v + (hs & 1) * H * NU * kWarp;
-            const float *xb = ring_x + (hs & 1) * H * NX * kWarp;
+            const float *vb = ring_v + (hs % 3) * kVSlot;
+            const float *xb = ring_x + (hs & 1) * kXSlot;
             const int t = hs * H + s;
             float v[NU], y[NX];
             float is = 0.f;
@@ -207,12 +218,9 @@ __global__ void __launch_bounds__(256) pair_rollout_kernel(const StepParams p) {
                 for (int s = 0; s < ns; ++s) J.add(cost_of(hs, s));
             }
         };
-        controls(0);
         pair_sync(bar_id);
         for (int hh = 0; hh < nh; ++hh) {
-            // half hh - 1 is read before half hh + 1 overwrites its ring slot
             if (hh >= 1) states(hh - 1);
-            if (hh + 1 < nh) controls(hh + 1);
             pair_sync(bar_id);
         }
         states(nh - 1);
@@ -376,8 +384,9 @@ size_t pair_rollout_smem_bytes(const mppi_ctx &c, int threads) {
         if constexpr (!kPairModel<D>) {
             return false;
         } else {
-            bytes = smem_bytes_for<D, C>(c) + sizeof(float) * static_cast<size_t>(threads / 64) *
-                                                  pair_ring_floats<D>();
+            bytes = smem_bytes_for<D, C>(c) +
+                    sizeof(float) * static_cast<size_t>(threads / (kPairRoles * kWarp)) *
+                        pair_ring_floats<D>();
             return true;
         }
     });
@@ -394,7 +403,7 @@ cudaError_t pair_rollout_prepare(const mppi_ctx &c) {
         } else {
             err = cudaFuncSetAttribute(pair_rollout_kernel<D, C>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(pair_rollout_smem_bytes(c, 256)));
+                                       static_cast<int>(pair_rollout_smem_bytes(c, 192)));
             return true;
         }
     });
