@@ -60,9 +60,11 @@ FLOPS_PER_ROLLOUT_STEP = {
 KERNEL_NAME = {
     "quadrotor": "quad_pair_kernel<true,false> (one sample per thread; dynamics, two noise and "
                  "a cost warp per 32 samples)",
-    "cartpole": "rollout_kernel<CartpoleDyn, QuadraticCost<4,1>>",
+    "cartpole": "pair_rollout_kernel<CartpoleDyn, QuadraticCost<4,1>> (dynamics, noise and "
+                "cost warps per 32 samples)",
     "bicycle": "bicycle_mlp_f32_kernel (four lanes per sample, FP32 CUDA cores)",
-    "diffdrive": "rollout_kernel<DiffDriveDyn, GoalCostmapCost>",
+    "diffdrive": "pair_rollout_kernel<DiffDriveDyn, GoalCostmapCost> (dynamics, noise and "
+                 "cost warps per 32 samples)",
 }
 # FP32 pipe: 128 FP32 lanes per SM, 2 flops per FMA.
 FP32_LANES_PER_SM = 128
