@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Bar (see the tolerance derivation in the design doc):
+Bar (the tolerances follow from FP32 rounding of the costs and the update):
   * Philox words bit-exact; normals within 8 ulp(|z|) + 2^-22;
   * u_new within 1e-4 * sigma_j of the oracle for every (t, j) (FP32 path);
   * stage-isolated: GPU weights / statistics from the GPU's own S_k agree with
