@@ -207,10 +207,11 @@ MPPI_API mppi_status mppi_set_stream(mppi_ctx *ctx, void *cuda_stream);
 MPPI_API mppi_status mppi_step(mppi_ctx *ctx, const float *x0_d, const float *u_nom_d,
                       float *u_new_d, float *weights_d, float *stats_d, float *costs_d);
 
-/* Same iteration from HOST buffers: copies x0_h and u_nom_h to the device,
- * runs mppi_step, copies u_new_h [T*nu] (and stats_h [4] unless NULL) back and
- * synchronises the stream before returning.  Pinned host memory gives
- * asynchronous copies; pageable memory works too. */
+/* Same iteration from HOST buffers (any host memory): stages x0_h and
+ * u_nom_h in a context-owned pinned buffer, copies them to the device once,
+ * runs mppi_step with u_new and the statistics written by the kernels
+ * straight into that (device-mapped) pinned buffer, synchronises the stream
+ * and copies u_new_h [T*nu] (and stats_h [4] unless NULL) out of it. */
 MPPI_API mppi_status mppi_step_host(mppi_ctx *ctx, const float *x0_h, const float *u_nom_h,
                            float *u_new_h, float *stats_h);
 

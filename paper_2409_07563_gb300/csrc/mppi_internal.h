@@ -104,7 +104,8 @@ struct mppi_ctx {
     float *d_dyn = nullptr, *d_cost = nullptr, *d_map = nullptr;
     int map_h = 0, map_w = 0;
     mppi::Scratch scr;
-    float *io_host = nullptr;           // pinned mirror of scr.io for mppi_step_host (first use)
+    float *io_host = nullptr;           // pinned, mapped staging for mppi_step_host (first use)
+    float *io_host_dev = nullptr;       // its device address
     mppi::LaunchPlan plan;
     cudaStream_t stream = nullptr;
     int device = 0, num_sms = 0;
