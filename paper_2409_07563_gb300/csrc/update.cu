@@ -126,9 +126,20 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
     for (int el = threadIdx.x; el < 4 * Q; el += blockDim.x) {
         const int q = el / 4, j = q / QT, t = 4 * (q % QT) + el % 4;
         if (t >= p.T) continue;
+        // chunk partials added in chunk order; the loads of eight chunks are
+        // issued together so their latencies overlap
+        const int ny = static_cast<int>(gridDim.y);
         float sum = 0.f;
-        for (int c = 0; c < static_cast<int>(gridDim.y); ++c)
-            sum += __ldcg(p.upartials + (static_cast<size_t>(c) * Q) * 4 + el);
+        int c = 0;
+        for (; c + 8 <= ny; c += 8) {
+            float v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                v[i] = __ldcg(p.upartials + (static_cast<size_t>(c + i) * Q) * 4 + el);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) sum += v[i];
+        }
+        for (; c < ny; ++c) sum += __ldcg(p.upartials + (static_cast<size_t>(c) * Q) * 4 + el);
         const int o = t * NU + j;
         p.u_new[o] = p.u_nom[o] + p.gamma * sum;  // gamma = 1: u_nom + sum exactly
     }
