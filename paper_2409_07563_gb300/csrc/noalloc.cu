@@ -159,6 +159,9 @@ __global__ void __launch_bounds__(kNaThreads) na_update_kernel(const NaParams p,
         const int q = q0 + threadIdx.x / 4;
         if (q < Q) part[(blockIdx.y * Q + q) * 4 + threadIdx.x % 4] = v;
     }
+    // the barrier orders every writer's partial before thread 0's device-scope
+    // fence (cumulative), and so before the ticket
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         s_last = atomicAdd(tickets + 1, 1u) == gridDim.x * gridDim.y - 1;

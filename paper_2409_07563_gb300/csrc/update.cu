@@ -113,6 +113,9 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
         if (q < Q)
             p.upartials[(static_cast<size_t>(blockIdx.y) * Q + q) * 4 + threadIdx.x % 4] = v;
     }
+    // the barrier orders every writer's partial before thread 0's device-scope
+    // fence (cumulative), and so before the ticket
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned int ticket = atomicAdd(p.tickets + 1, 1u);
