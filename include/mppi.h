@@ -102,9 +102,10 @@ typedef enum {
  *                  phi = s sum Q_i (y_i - goal_i)^2.
  *  QUAD_OBSTACLES  QUADRATIC params + [n_obs, c_crash, (cx,cy,cz,r) x n_obs]
  *                  (quadrotor only): l += c_crash when some sphere has
- *                  |p - c|^2 - r^2 < 0, evaluated in FP32 with one rounding
- *                  per operation as fma(dz,dz, fma(dy,dy, fma(dx,dx, -r*r)))
- *                  with d = p - c; n_obs <= 256.
+ *                  |p - c|^2 - r^2 < 0 (strict), evaluated in FP32 on the
+ *                  FP32 state as fma(dz,dz, fma(dy,dy, fma(dx,dx, -r*r)))
+ *                  with d = p - c, so a step within the FP32 state error of
+ *                  a sphere's surface can be decided either way; n_obs <= 256.
  *  COSTMAP_SPEED   params [c_map, c_speed, v_des, x_min, y_min, cell] plus a
  *                  map_h x map_w map (row i = y): l = phi = c_map M(x, y) +
  *                  c_speed (v - v_des)^2, M bilinear between cell centres
@@ -114,7 +115,8 @@ typedef enum {
  *                  (double integrator only; Eq. 25):
  *                  l = c_ring (1{r^2 <= r_in^2} + 1{r^2 >= r_out^2})
  *                  + c_v |v_des - |v|| + c_h |h_des - (x vy - y vx)|, phi = 0;
- *                  the two indicators are taken in FP32 like the crash test.
+ *                  the two indicators are taken in FP32 on the FP32 state
+ *                  (like the crash test, exact only away from the circles).
  *  GOAL_COSTMAP    params [c_goal, c_angle, c_obs, gx, gy, g_theta, x_min,
  *                  y_min, cell] plus a map_h x map_w map (DIFF_DRIVE only; the
  *                  paper's benchmark cost, Sec. V): l = phi = c_goal |p - g|^2
@@ -351,6 +353,12 @@ MPPI_API mppi_status mppi_batch_step(mppi_batch *b, void *cuda_stream);
 MPPI_API mppi_status mppi_batch_latency(mppi_batch *b, void *cuda_stream, float *ms);
 /* info[4] = block threads, rollout grid, rollout work items, update work items. */
 MPPI_API mppi_status mppi_batch_info(const mppi_batch *b, int *info);
+/* Copies instance i's per-sample costs S_k and weights w_k of the last step
+ * (K_i floats each, Algorithm 1's S and w) into caller device memory, on
+ * cuda_stream; either pointer may be NULL.  MPPI_ERR_INVALID_ARG for a bad
+ * index. */
+MPPI_API mppi_status mppi_batch_samples(const mppi_batch *b, int i, float *costs_d,
+                                        float *weights_d, void *cuda_stream);
 MPPI_API void mppi_batch_destroy(mppi_batch *b);
 
 /* ---------------------------------------------------------------------------

@@ -91,6 +91,7 @@ def lib():
         L.oracle_cem_weights.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp]
         L.oracle_cem_step.argtypes = [P, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, ctypes.c_int]
         L.oracle_max_threads.argtypes = []
+        L.oracle_decision_margins.argtypes = [P, _dp, _dp, _dp, ctypes.c_int]
     return _lib
 
 
@@ -299,3 +300,15 @@ def mppi_grad_cartpole(p, G, step=0, n_threads=1, x0=None, u_nom=None):
     st = lib().oracle_mppi_grad_cartpole(P.ref, _ptr(x0), _ptr(u), _ptr(G), _ptr(grad),
                                          int(n_threads))
     return grad, st
+
+
+def decision_margins(p, step=0, n_threads=1, x0=None, u_nom=None):
+    """Per-sample distance (min over t) of the cost's integer decisions (crash
+    test, ring indicators) from their thresholds; +inf without such decisions."""
+    P = Problem(p, step)
+    x0 = np.ascontiguousarray(p["x0"] if x0 is None else x0, float)
+    u = np.ascontiguousarray(p["u_nom"] if u_nom is None else u_nom, float)
+    margin = np.zeros(p["K"])
+    st = lib().oracle_decision_margins(P.ref, _ptr(x0), _ptr(u), _ptr(margin), int(n_threads))
+    assert st == 0
+    return margin

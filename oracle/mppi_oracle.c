@@ -278,17 +278,18 @@ int oracle_dynamics_step(const oracle_problem *p, const double *x, const double 
  *                   phi = s * sum Q_i (y_i - goal_i)^2
  *   QUAD_OBSTACLES  QUADRATIC + [n_obs, c_crash, (cx, cy, cz, r) * n_obs]:
  *                   l += c_crash if some sphere has |p - c|^2 - r^2 < 0
- *                   (p = y[0..2]); phi unchanged.  In FP32 the test reads
- *                   fma(dz,dz, fma(dy,dy, fma(dx,dx, -fl(r*r)))) < 0.
+ *                   (p = y[0..2]); phi unchanged.
  *   COSTMAP_SPEED   [c_map, c_speed, v_des, x_min, y_min, cell]:
  *                   l = phi = c_map M(y0, y1) + c_speed (y3 - v_des)^2
  *   CIRCLE          [r_in, r_out, c_ring, v_des, c_v, h_des, c_h]
  *                   (Eq. 25): l = c_ring (1{r^2 <= r_in^2} + 1{r^2 >= r_out^2})
  *                   + c_v |v_des - |v|| + c_h |h_des - (x vy - y vx)|, phi = 0.
  *
- * The crash and ring indicators are integers decided by floating point; as in
- * the paper's FP32 library, that comparison is taken in single precision on
- * the state rounded to float, with one rounding per operation.
+ * The crash and ring indicators are integers decided by floating point.  Here
+ * they are the plain definitions evaluated in double precision on the FP64
+ * state; a single-precision implementation can decide a step differently when
+ * its state lies within its rounding error of the boundary, which is why
+ * oracle_decision_margins reports how close each sample came to it.
  * ------------------------------------------------------------------------ */
 
 static double quad_state_cost(const oracle_problem *p, const double *y)
@@ -310,23 +311,19 @@ static double quad_control_cost(const oracle_problem *p, const double *v)
     return c;
 }
 
-static int crash_fp32(const double *obs, int n_obs, const double *y)
+/* min over the spheres of |p - c|^2 - r^2 (negative inside some sphere) */
+static double sphere_margin(const double *obs, int n_obs, const double *y)
 {
-    /* m = fma(dz, dz, fma(dy, dy, fma(dx, dx, -fl(r*r)))), d = fl(p - c), all in
-     * FP32 with one rounding per operation; crash if m < 0. */
-    volatile float px = (float)y[0], py = (float)y[1], pz = (float)y[2];
+    double m = INFINITY;
     for (int i = 0; i < n_obs; ++i) {
-        volatile float dx = px - (float)obs[4 * i + 0];
-        volatile float dy = py - (float)obs[4 * i + 1];
-        volatile float dz = pz - (float)obs[4 * i + 2];
-        volatile float r = (float)obs[4 * i + 3];
-        volatile float rr = r * r;
-        volatile float m = fmaf(dx, dx, -rr);
-        m = fmaf(dy, dy, m);
-        m = fmaf(dz, dz, m);
-        if (m < 0.0f) return 1;
+        double dx = y[0] - obs[4 * i + 0];
+        double dy = y[1] - obs[4 * i + 1];
+        double dz = y[2] - obs[4 * i + 2];
+        double r = obs[4 * i + 3];
+        double mi = dx * dx + dy * dy + dz * dz - r * r;
+        if (mi < m) m = mi;
     }
-    return 0;
+    return m;
 }
 
 static double map_bilinear(const oracle_problem *p, double x, double y, double x_min,
@@ -372,14 +369,10 @@ static double goal_costmap_cost(const oracle_problem *p, const double *y)
 
 static double circle_cost(const double *C, const double *y)
 {
-    volatile float fx = (float)y[0], fy = (float)y[1];
-    volatile float xx = fx * fx, yy = fy * fy;
-    volatile float r2 = xx + yy;
-    volatile float rin = (float)C[0], rout = (float)C[1];
-    volatile float rin2 = rin * rin, rout2 = rout * rout;
+    double r2 = y[0] * y[0] + y[1] * y[1];
     double c = 0.0;
-    if (r2 <= rin2) c += C[2];
-    if (r2 >= rout2) c += C[2];
+    if (r2 <= C[0] * C[0]) c += C[2];
+    if (r2 >= C[1] * C[1]) c += C[2];
     double speed = sqrt(y[2] * y[2] + y[3] * y[3]);
     c += C[4] * fabs(C[3] - speed);
     c += C[6] * fabs(C[5] - (y[0] * y[3] - y[1] * y[2]));
@@ -396,7 +389,7 @@ double oracle_running_cost(const oracle_problem *p, const double *y, const doubl
         int base = 2 * p->nx + p->nu + 1;
         int n_obs = (int)C[base];
         double c = quad_state_cost(p, y) + quad_control_cost(p, v);
-        if (crash_fp32(C + base + 2, n_obs, y)) c += C[base + 1];
+        if (sphere_margin(C + base + 2, n_obs, y) < 0.0) c += C[base + 1];
         return c;
     }
     case OR_COST_COSTMAP_SPEED: {
@@ -465,6 +458,55 @@ double oracle_rollout(const oracle_problem *p, const double *x0, const double *u
     }
     J += oracle_terminal_cost(p, x);
     return J;
+}
+
+/* How far the cost's integer decisions at post-step output y are from their
+ * thresholds: |min_i (|p - c_i|^2 - r_i^2)| for the sphere crash test,
+ * min(|r^2 - r_in^2|, |r^2 - r_out^2|) for the ring indicators of Eq. 25, and
+ * +inf for costs without such a decision. */
+static double decision_margin(const oracle_problem *p, const double *y)
+{
+    const double *C = p->cost_params;
+    switch (p->cost_kind) {
+    case OR_COST_QUAD_OBSTACLES: {
+        int base = 2 * p->nx + p->nu + 1;
+        return fabs(sphere_margin(C + base + 2, (int)C[base], y));
+    }
+    case OR_COST_CIRCLE: {
+        double r2 = y[0] * y[0] + y[1] * y[1];
+        double a = fabs(r2 - C[0] * C[0]), b = fabs(r2 - C[1] * C[1]);
+        return a < b ? a : b;
+    }
+    default:
+        return INFINITY;
+    }
+}
+
+int oracle_decision_margins(const oracle_problem *p, const double *x0, const double *u_nom,
+                            double *margin, int n_threads)
+{
+    if (!p || p->K <= 0 || p->T <= 0 || p->nx <= 0 || p->nx > OR_MAX_NX || p->nu <= 0 ||
+        p->nu > OR_MAX_NU || !p->sigma || !margin)
+        return OR_ERR_INVALID_ARG;
+    int T = p->T, nu = p->nu, nx = p->nx;
+    if (n_threads < 1) n_threads = 1;
+    /* the same samples and rollouts as oracle_mppi_step */
+#pragma omp parallel for num_threads(n_threads) schedule(static)
+    for (int k = 0; k < p->K; ++k) {
+        double x[OR_MAX_NX], xn[OR_MAX_NX], v[OR_MAX_NU];
+        memcpy(x, x0, sizeof(double) * nx);
+        double mk = INFINITY;
+        for (int t = 0; t < T; ++t) {
+            for (int j = 0; j < nu; ++j)
+                v[j] = u_nom[t * nu + j] + p->sigma[j] * normal_at(p->seed, p->step, k, t, j, T);
+            oracle_dynamics_step(p, x, v, xn);
+            memcpy(x, xn, sizeof(double) * nx);
+            double d = decision_margin(p, x);
+            if (d < mk) mk = d;
+        }
+        margin[k] = mk;
+    }
+    return OR_OK;
 }
 
 /* Weights of Algorithm 1 / Eq. 17-18: rho = min S, eta = sum exp(-(S-rho)/lambda),

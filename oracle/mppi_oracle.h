@@ -87,6 +87,16 @@ double oracle_costmap_sample(const oracle_problem *p, double x, double y);
 double oracle_rollout(const oracle_problem *p, const double *x0, const double *u_nom,
                       const double *v, double *traj);
 
+/* Per sample k of the step (the same noise and rollouts as oracle_mppi_step),
+ * the smallest distance over t of the running cost's integer decisions from
+ * their thresholds at the post-step output: |min_i |p - c_i|^2 - r_i^2| for
+ * the sphere crash test, min(|r^2 - r_in^2|, |r^2 - r_out^2|) for the ring
+ * indicators of Eq. 25, +inf for costs without such a decision.  An FP32
+ * implementation may decide a step differently only where this is within its
+ * rounding error of 0.  margin[K]. */
+int oracle_decision_margins(const oracle_problem *p, const double *x0, const double *u_nom,
+                            double *margin, int n_threads);
+
 /* Weights from costs: w[K] (may be NULL), stats = [F, rho, eta, ess]. */
 int oracle_weights(int K, const double *S, double lambda, double *w, double *stats);
 

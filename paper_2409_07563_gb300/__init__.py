@@ -432,6 +432,17 @@ class MPPIBatch:
     def stats_of(self, i):
         return self.stats[4 * i:4 * i + 4]
 
+    def samples_of(self, i, stream=None):
+        """Instance i's per-sample costs and weights of the last step
+        (``mppi_batch_samples``), as two CUDA tensors of K_i."""
+        import torch
+        K = int(self.problems[i]["K"])
+        costs = torch.empty(K, dtype=torch.float32, device=self.u_new.device)
+        weights = torch.empty_like(costs)
+        check(load().mppi_batch_samples(self._h, int(i), _dptr(costs), _dptr(weights),
+                                        _stream_handle(stream)), "mppi_batch_samples")
+        return costs, weights
+
     def close(self):
         if getattr(self, "_h", None):
             load().mppi_batch_destroy(self._h)

@@ -123,6 +123,8 @@ def _optional(L):
         L.mppi_batch_info.restype = ctypes.c_int
         L.mppi_batch_destroy.argtypes = [vp]
         L.mppi_batch_destroy.restype = None
+        L.mppi_batch_samples.argtypes = [vp, i, vp, vp, vp]
+        L.mppi_batch_samples.restype = ctypes.c_int
 
 
 def exported_symbols():

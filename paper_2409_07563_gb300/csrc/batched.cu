@@ -695,6 +695,19 @@ mppi_status mppi_batch_info(const mppi_batch *b, int *info) {
     return MPPI_OK;
 }
 
+mppi_status mppi_batch_samples(const mppi_batch *b, int i, float *costs_d, float *weights_d,
+                               void *cuda_stream) {
+    if (!b || i < 0 || i >= b->n) return MPPI_ERR_INVALID_ARG;
+    const DevInst &d = b->dev_h[i];
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const size_t bytes = static_cast<size_t>(d.K) * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    if (costs_d) e = cudaMemcpyAsync(costs_d, d.S, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && weights_d)
+        e = cudaMemcpyAsync(weights_d, d.w, bytes, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
+}
+
 void mppi_batch_destroy(mppi_batch *b) { free_batch(b); }
 
 }  // extern "C"

@@ -1,17 +1,18 @@
 """Batched launch (mppi_batch_*) against the FP64 oracle, instance by instance.
 
 Each instance is an independent MPPI problem (own seed, x0, K, T, model); the
-bar is the single-instance one: u_new within 1e-4 sigma_j, statistics from
-the same weights.  Covers a ragged mixed batch (K not a multiple of any tile,
-K = 1, T from 1 to 200), two consecutive steps (per-instance counters), every
-autotuner candidate block size, and the full 256-instance workload.
+bar is the single-instance one: u_new within 1e-4 sigma_j, every sample's cost
+within the FP32 bound, weights and statistics from the same costs.  Covers a
+ragged mixed batch (K not a multiple of any tile, K = 1, T from 1 to 200), two
+consecutive steps (per-instance counters), every autotuner candidate block
+size, and the full 256-instance workload with every instance compared.
 """
 import numpy as np
 import pytest
 
 import oracle
 import workloads as W
-from _util import as_f32_problem, n_threads
+from _util import as_f32_problem, check_costs, cost_propagation, n_threads
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -40,15 +41,30 @@ def ragged_batch():
 
 
 def check_instance(b, i, p, step=0):
-    o = oracle.mppi_step(p, step=step, n_threads=n_threads())
+    """Every sample's cost (check_costs); u_new within 1e-4 sigma plus what the
+    cost differences move the oracle's own update by (cost_propagation); the
+    update, weights and statistics from the GPU's own costs."""
+    o = oracle.mppi_step(p, step=step, n_threads=n_threads(), want_eps=True)
     g = b.u_new_of(i).cpu().numpy().astype(np.float64)
     st = b.stats_of(i).cpu().numpy().astype(np.float64)
+    gS, gw = (t.cpu().numpy().astype(np.float64) for t in b.samples_of(i))
+    max_rel, flipped = check_costs(p, gS, o["S"], step=step)
     sig = p["sigma"]
     err = np.abs(g - o["u_new"])
-    assert np.all(err <= 1e-4 * sig[None, :]), (i, p["name"], np.max(err / sig))
-    assert st[1] == pytest.approx(o["stats"][1], rel=1e-5, abs=1e-3)      # rho
-    assert st[0] == pytest.approx(o["stats"][0], rel=1e-5, abs=1e-3)      # F
-    assert st[3] == pytest.approx(o["stats"][3], rel=2e-3)                # ESS
+    prop = cost_propagation(p, gS, o["S"], o["eps"])
+    assert np.all(err <= 1e-4 * sig[None, :] + prop), (i, p["name"], np.max(err / sig))
+    # the update stage from the GPU's own costs
+    w_iso, _, _ = oracle.weights(gS, p["lam"])
+    u_iso = p["u_nom"] + np.einsum("k,ktj->tj", w_iso, o["eps"])
+    assert np.all(np.abs(g - u_iso) <= 1e-5 * sig[None, :]), (i, p["name"])
+    # statistics and weights from the GPU's own costs (the FP32 reduction)
+    w_ref, st_ref, _ = oracle.weights(gS, p["lam"])
+    x = (gS - st_ref[1]) / p["lam"]
+    assert np.all(np.abs(gw - w_ref) <= 2e-5 * (1 + np.abs(x)) * w_ref + 1e-9), (i, p["name"])
+    assert st[1] == st_ref[1]                                               # rho
+    assert st[0] == pytest.approx(st_ref[0], rel=1e-5, abs=1e-3)            # F
+    assert st[3] == pytest.approx(st_ref[3], rel=2e-3)                      # ESS
+    return float(np.max(err / sig)), max_rel, int(flipped.sum()), float(np.max(prop / sig))
 
 
 @pytest.mark.parametrize("threads", [64, 128, 256])
@@ -70,14 +86,21 @@ def test_ragged_batch_matches_oracle(m, threads):
 
 
 def test_autotuned_full_batch_matches_oracle(m):
+    """The 256-instance workload, every instance compared with the oracle."""
     probs = [as_f32_problem(p) for p in W.batched()]
     b = m.MPPIBatch(probs)
     info = b.info()
     assert info["block_threads"] in (64, 128, 256)
     b.step()
     torch.cuda.synchronize()
-    rng = np.random.default_rng(0)
-    sample = sorted(set([0, 127, 128, 255] + list(rng.integers(0, 256, 28))))
-    for i in sample:
-        check_instance(b, int(i), probs[int(i)])
+    worst = (0.0, 0.0, 0, 0.0)
+    over = []
+    for i in range(len(probs)):
+        e, r, f, c = check_instance(b, i, probs[i])
+        worst = (max(worst[0], e), max(worst[1], r), worst[2] + f, max(worst[3], c))
+        if e > 1e-4:
+            over.append((i, e, c))
+    print(f"\n256 instances: max |du|/sigma {worst[0]:.2e}, max cost rel {worst[1]:.2e}, "
+          f"flipped samples {worst[2]}, max cost-propagated {worst[3]:.2e}; above 1e-4 sigma "
+          f"(all explained by FP32 cost resolution): {over}")
     b.close()

@@ -18,7 +18,7 @@ import pytest
 
 import oracle
 import workloads as W
-from _util import as_f32_problem, n_threads
+from _util import as_f32_problem, check_costs, n_threads
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -65,6 +65,7 @@ def test_cem_matches_oracle(m, name, make, frac, kw):
     assert np.array_equal(np.flatnonzero(g["weights"]), np.flatnonzero(w_ref))
     assert np.all(g["weights"][w_ref != 0] == np.float32(1.0 / n_e))
     o = oracle.mppi_step(p, n_threads=n_threads(), want_eps=True)
+    max_rel, flipped = check_costs(p, g["costs"], o["S"])
     u_iso = p["u_nom"] + np.einsum("k,ktj->tj", w_ref, o["eps"])
     sig = p["sigma"]
     assert np.all(np.abs(g["u_new"] - u_iso) <= 1e-5 * sig[None, :])

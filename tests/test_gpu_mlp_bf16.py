@@ -2,9 +2,10 @@
 oracle.  BF16 operands round the MLP inputs, weights and activations to 8
 significant bits, so this path has no 1e-4 sigma bound; what is checked:
 
-  * per-sample trajectory costs: median relative error <= 1e-3, 99th
-    percentile <= 1e-2 (BF16 rounding of a residual that is ~10% of the
-    dynamics, integrated over the horizon);
+  * every sample's trajectory cost within 1e-3 relative of the oracle's
+    (BF16 rounding, unit roundoff 2^-9, of a residual that moves the state by
+    about 0.4 dt per step, aligned over the horizon; derivation in
+    tests/_util.py), and the median within 1e-4;
   * stage-isolated weighting and update from the GPU's own costs exactly as
     for the FP32 path (those stages are FP32);
   * end to end with spread weights (lambda = 100): |du| <= 0.05 sigma.
@@ -15,7 +16,7 @@ import pytest
 
 import oracle
 import workloads as W
-from _util import as_f32_problem, n_threads
+from _util import BF16_COST_REL, as_f32_problem, check_costs, n_threads
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -47,8 +48,8 @@ def test_bf16_mlp_costs_and_update(m, K, T, lam):
     rel = np.abs(g["costs"] - o["S"]) / np.maximum(1.0, np.abs(o["S"]))
     print(f"\nBF16 MLP K={K} T={T} lam={lam}: S rel err median {np.median(rel):.2e} "
           f"p99 {np.percentile(rel, 99):.2e} max {rel.max():.2e}")
-    assert np.median(rel) <= 1e-3
-    assert np.percentile(rel, 99) <= 1e-2
+    check_costs(p, g["costs"], o["S"], bf16=True)
+    assert np.median(rel) <= 1e-4
     # weighting and update stages from the GPU's own costs (FP32 stages)
     w_ref, st_ref, _ = oracle.weights(g["costs"], lam)
     x = (g["costs"] - st_ref[1]) / lam
@@ -66,7 +67,7 @@ def test_bf16_and_fp32_paths_agree_on_costs(m):
     g16 = run(m, p, m.MPPI_PREC_BF16_MLP)
     g32 = run(m, p, m.MPPI_PREC_FP32)
     rel = np.abs(g16["costs"] - g32["costs"]) / np.maximum(1.0, np.abs(g32["costs"]))
-    assert np.median(rel) <= 1e-3
+    assert rel.max() <= BF16_COST_REL
 
 
 def run_opts(m, p, precision, **kw):
@@ -87,9 +88,7 @@ def test_bf16_mlp_warp_pairs_block_sizes(m, bt, K, T):
     p = as_f32_problem(W.bicycle_mlp(K=K, T=T, lam=100.0))
     g = run_opts(m, p, m.MPPI_PREC_BF16_MLP, block_threads=bt)
     o = oracle.mppi_step(p, n_threads=n_threads(), want_eps=True)
-    rel = np.abs(g["costs"] - o["S"]) / np.maximum(1.0, np.abs(o["S"]))
-    assert np.median(rel) <= 1e-3
-    assert rel.max() <= 2e-2
+    check_costs(p, g["costs"], o["S"], bf16=True)
     w_ref, st_ref, _ = oracle.weights(g["costs"], 100.0)
     u_iso = p["u_nom"] + np.einsum("k,ktj->tj", w_ref, o["eps"])
     assert np.all(np.abs(g["u_new"] - u_iso) <= 1e-5 * p["sigma"][None, :])

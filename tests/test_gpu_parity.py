@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 import workloads as W
-from _util import as_f32_problem, n_threads, with_
+from _util import as_f32_problem, check_costs, cost_propagation, n_threads, with_
 
 pytestmark = pytest.mark.gpu
 
@@ -44,14 +44,25 @@ def run_gpu(m, p, step=0, ctl=None, **kw):
     return res, ctl
 
 
-def compare(p, g, step=0, tol_sigma=1e-4, check_S=True, cost_resolution=False):
+def compare(p, g, step=0, tol_sigma=1e-4, check_S=True, cost_resolution=False,
+            well_conditioned=False):
     """End-to-end and stage-isolated comparison; returns diagnostics.
 
-    cost_resolution=True widens the end-to-end bound by the first-order effect
-    of FP32 cost resolution, |du| <= 2 D / lambda * sum_k w_k |eps_k| with
-    D = 2^-17 max|S_k| (64 ulp of the largest cost), and checks that the
-    per-sample cost differences stay inside D (so the widening is not hiding
-    rollout drift)."""
+    The GPU result is compared stage by stage:
+      * every sample's cost against the oracle's (``check_costs``: (T + 8) u
+        relative; whole crash / ring jumps only where the oracle's trajectory
+        passes within the FP32 error bound of the decision boundary);
+      * weights, statistics and update from the GPU's own costs against the
+        oracle's FP64 weighting and noise (1e-5 sigma);
+      * end to end: |u_gpu - u_oracle| <= 1e-4 sigma + |u(S_gpu) - u(S_oracle)|,
+        the second term being the oracle's own update moved by the (bounded)
+        cost differences (``cost_propagation``).  well_conditioned=True
+        (the configurations at full size) requires the plain 1e-4 sigma bar
+        with no such allowance.
+
+    cost_resolution=True also checks that every cost difference stays inside
+    D = 2^-17 max|S_k| (64 ulp of the largest cost): the ill-conditioned
+    cases' widening then comes from FP32 resolution, not rollout drift."""
     o = oracle.mppi_step(p, step=step, n_threads=n_threads(), want_eps=True)
     lam = p["lam"]
     sig = p["sigma"]
@@ -70,23 +81,30 @@ def compare(p, g, step=0, tol_sigma=1e-4, check_S=True, cost_resolution=False):
     err_iso = np.abs(g["u_new"] - u_iso)
     assert np.all(err_iso <= 1e-5 * sig[None, :] + 1e-7 * (sig[None, :] == 0)), \
         f"update stage: max err/sigma {np.max(err_iso / np.maximum(sig, 1e-30))}"
-    # per-sample costs
-    dS = np.abs(g["costs"] - o["S"])
+    # per-sample costs, every sample
+    flipped = np.zeros(K, bool)
+    max_rel = None
     if check_S:
-        rel = dS / np.maximum(1.0, np.abs(o["S"]))
-        assert np.median(rel) < 1e-5, np.median(rel)
-    # end to end
-    err = np.abs(g["u_new"] - o["u_new"])
-    ratio = np.max(err / np.maximum(sig[None, :], 1e-30))
-    diag = dict(max_err_over_sigma=float(ratio), ess=float(o["stats"][3]),
-                max_dS_over_lambda=float(np.max(dS) / lam),
-                argmin_same=bool(np.argmin(g["costs"]) == np.argmin(o["S"])))
-    bound = tol_sigma * sig[None, :]
+        max_rel, flipped = check_costs(p, g["costs"], o["S"], step=step)
+    dS = np.abs(g["costs"] - o["S"])
     if cost_resolution:
         D = 2.0**-17 * np.max(np.abs(o["S"]))
-        assert np.mean(dS <= D) >= 0.99, (np.max(dS), D)
-        bound = bound + 2 * D / lam * np.einsum("k,ktj->tj", o["w"], np.abs(o["eps"]))
-    assert np.all(err <= bound), diag
+        assert np.all(dS <= D), (np.max(dS), D)
+    # end to end
+    prop = cost_propagation(p, g["costs"], o["S"], o["eps"]) if check_S else 0.0
+    err = np.abs(g["u_new"] - o["u_new"])
+    sg = np.maximum(sig[None, :], 1e-30)
+    ratio = np.max(err / sg)
+    prop_ratio = float(np.max(prop / sg))
+    diag = dict(max_err_over_sigma=float(ratio), cost_propagated_over_sigma=prop_ratio,
+                ess=float(o["stats"][3]), max_cost_rel=max_rel, n_flipped=int(flipped.sum()),
+                max_dS_over_lambda=float(np.max(dS[~flipped], initial=0.0) / lam),
+                argmin_same=bool(np.argmin(g["costs"]) == np.argmin(o["S"])))
+    if well_conditioned:
+        assert np.all(err <= tol_sigma * sig[None, :]), diag
+    assert np.all(err <= tol_sigma * sig[None, :] + prop), diag
+    print(f"\n{p['name']}: max |du|/sigma {ratio:.2e} (cost-propagated {prop_ratio:.2e}), "
+          f"max cost rel {max_rel}, flipped {int(flipped.sum())}")
     return diag
 
 
@@ -120,7 +138,7 @@ def test_cartpole_config_full(m):
     p = as_f32_problem(W.cartpole())
     g, ctl = run_gpu(m, p)
     assert g["status"] == 0
-    compare(p, g)
+    compare(p, g, well_conditioned=True)
     # the next step uses the next counter value
     g1, _ = run_gpu(m, p, ctl=ctl)
     compare(p, g1, step=1)
@@ -141,7 +159,7 @@ def test_cartpole_spread_weights(m, lam):
 def test_quadrotor_config_full(m, variant):
     p = as_f32_problem(W.quadrotor())
     g, _ = run_gpu(m, p, rollout_variant=variant)
-    compare(p, g)
+    compare(p, g, well_conditioned=True)
 
 
 @pytest.mark.parametrize("variant", [1, 2, 3, 4])
@@ -209,7 +227,7 @@ def test_bicycle_mlp_fp32_config_full(m, variant):
     """Automatic (four lanes per sample) and one sample per thread."""
     p = as_f32_problem(W.bicycle_mlp())
     g, _ = run_gpu(m, p, rollout_variant=variant)
-    compare(p, g)
+    compare(p, g, well_conditioned=True)
 
 
 @pytest.mark.parametrize("bt", [32, 64, 96, 128, 256])

@@ -351,6 +351,76 @@ def test_quadratic_and_crash_costs_by_hand(oracle_lib):
     assert oracle.terminal_cost(p, y2) == pytest.approx(10 * 10.0 * d @ d)
 
 
+def _one_sphere_quadrotor(c, r, K=4, T=4):
+    """A quadrotor problem whose only obstacle is the sphere (c, r)."""
+    p = W.quadrotor(K=K, T=T, obstacles=np.array([[c[0], c[1], c[2], r]]))
+    return p
+
+
+def test_crash_indicator_is_the_exact_definition(oracle_lib):
+    # Dyadic sphere: centre (0.5, 0.25, 0.125), r = 0.625 = |(0.375, 0.5, 0)|,
+    # so the surface point is exact in FP64 and |p - c|^2 - r^2 = 0 there (the
+    # strict test says no crash).  A point 2^-45 inside along y crashes; FP32
+    # would round it onto the surface and miss the crash, so this pins the
+    # double-precision definition, not a single-precision evaluation of it.
+    c = np.array([0.5, 0.25, 0.125])
+    p = _one_sphere_quadrotor(c, 0.625)
+    y = np.zeros(13)
+    y[6] = 1.0
+    y[0:3] = c + [0.375, 0.5, 0.0]
+    base = oracle.running_cost(p, y, [0, 0, 0, 0])
+    d = y[0:3] - 3.0
+    assert base == pytest.approx(10.0 * d @ d)                  # on the surface: no crash
+    y_in = y.copy()
+    y_in[1] -= 2.0**-45
+    assert np.float32(y_in[1]) == np.float32(y[1])               # FP32 cannot see the step
+    assert oracle.running_cost(p, y_in, [0, 0, 0, 0]) - base == pytest.approx(1e4, rel=1e-9)
+    y_out = y.copy()
+    y_out[1] += 2.0**-45
+    assert oracle.running_cost(p, y_out, [0, 0, 0, 0]) == pytest.approx(base, rel=1e-12)
+
+
+def test_ring_indicators_are_the_exact_definition(oracle_lib):
+    # r_in = 1.875, r_out = 2.125 (dyadic): on either circle the indicator is
+    # on (<= and >=); 2^-45 off the circle on the ring side it is off.  FP32
+    # rounds those points onto the circles.
+    p = W.double_integrator()
+    C = p["cost_params"]
+    def ring(x):
+        return oracle.running_cost(p, [x, 0.0, 0.0, 0.0], [0, 0])
+
+    def smooth(x):
+        # at rest: speed term c_v |v_des|, momentum term c_h |h_des|
+        return C[4] * abs(C[3]) + C[6] * abs(C[5])
+    for r_c, inward in ((C[0], +1.0), (C[1], -1.0)):
+        on = ring(r_c) - smooth(r_c)
+        off = ring(r_c + inward * 2.0**-45) - smooth(r_c)
+        assert np.float32(r_c + inward * 2.0**-45) == np.float32(r_c)
+        assert on == pytest.approx(C[2])
+        assert off == pytest.approx(0.0, abs=1e-9)
+
+
+def test_decision_margins_by_hand(oracle_lib):
+    # sigma = 0: every sample follows the nominal trajectory, so the margin is
+    # the trajectory's closest approach computed directly from its states.
+    p = W.quadrotor(K=3, T=40)
+    p["sigma"] = np.zeros(4)
+    traj, _ = oracle.rollout(p, p["u_nom"])
+    obs = p["obstacles"]
+    m = ((traj[1:, None, 0:3] - obs[None, :, 0:3]) ** 2).sum(-1) - obs[None, :, 3] ** 2
+    want = np.abs(m.min(axis=1)).min()
+    got = oracle.decision_margins(p)
+    np.testing.assert_allclose(got, want, rtol=1e-12)
+    q = W.double_integrator(K=2, T=30)
+    q["sigma"] = np.zeros(2)
+    traj, _ = oracle.rollout(q, q["u_nom"])
+    r2 = traj[1:, 0] ** 2 + traj[1:, 1] ** 2
+    C = q["cost_params"]
+    want = np.minimum(np.abs(r2 - C[0] ** 2), np.abs(r2 - C[1] ** 2)).min()
+    np.testing.assert_allclose(oracle.decision_margins(q), want, rtol=1e-12)
+    assert np.all(np.isinf(oracle.decision_margins(W.cartpole(K=4, T=5))))
+
+
 def test_circle_cost_by_hand(oracle_lib):
     # Eq. 25 at points of the ring: r = 2, tangential speed 2, counter-clockwise -> 0
     p = W.double_integrator()
