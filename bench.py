@@ -9,8 +9,18 @@ T=150, lambda=0.5).  Metric: rollout-steps/s = K*T / step time.
              resident in HBM, L2 flushed (256 MiB write) before every step
   e2e        the same step through mppi_step_host(): pinned host inputs copied
              in and u_new + statistics copied out every step, wall-clock
-  roofline   rollout kernel (the dominant one) against the FP32 pipe peak
-  cpu_baseline  the FP64 C oracle on this host's cores, bounded sample
+  roofline   rollout kernel (the dominant one) against the FP32 pipe peak,
+             measured by the library's FMA probe (the derived figure beside it)
+  graph_replay  the same step captured in a CUDA graph: p50 / p99 of 1000
+             replays after 50 warm-ups, L2 flushed before each
+  cpu_baseline  the FP64 C oracle on this host's cores (all cores, and one
+             thread on a bounded sample)
+  oracle_err the oracle leg: every benchmarked form's GPU result (one untimed
+             step on the bench inputs) against the FP64 oracle; per form in
+             extensions.*.oracle_err, all forms in oracle_err_all
+  extensions configuration 0 (cart-pole), the batched, differentiable,
+             multi-iteration, CEM and BF16-MLP forms, the paper's diff-drive
+             benchmark over its K sweep, a quadrotor K sweep
 
 ``--impl reference`` times the oracle alone as the reference arm.
 Multi-GPU (torchrun): independent replicas, one per rank (weak scaling).
@@ -188,9 +198,10 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(p, budget_s=12.0):
-    """The FP64 oracle as it stands, all host cores, full workload steps until
-    the time budget is spent (at least one step)."""
+def cpu_baseline(p, budget_s=12.0, single_budget_s=6.0):
+    """The FP64 oracle as it stands on this host: all cores (OpenMP over
+    samples), full workload steps until the time budget is spent (at least one
+    step); and one thread on a bounded sample of the same workload."""
     import oracle
     threads = os.cpu_count() or 1
     oracle.mppi_step(dict(p, K=min(p["K"], 64)), n_threads=threads)  # build + warm
@@ -202,10 +213,124 @@ def cpu_baseline(p, budget_s=12.0):
         el = time.perf_counter() - t0
         if el >= budget_s or n >= 1000:
             break
-    return {"value": p["K"] * p["T"] * n / el, "unit": UNIT, "cores": threads,
-            "kind": "oracle",
-            "sample": f"{n} full oracle step(s) of {p['name']} (FP64, OpenMP over samples), "
-                      f"{el:.1f} s"}
+    out = {"value": p["K"] * p["T"] * n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{n} full oracle step(s) of {p['name']} (FP64, OpenMP over samples), "
+                     f"{el:.1f} s"}
+    ks = min(p["K"], 512)
+    ps = dict(p, K=ks)
+    t0 = time.perf_counter()
+    n1 = 0
+    while True:
+        oracle.mppi_step(ps, step=n1, n_threads=1)
+        n1 += 1
+        el1 = time.perf_counter() - t0
+        if el1 >= single_budget_s or n1 >= 1000:
+            break
+    out["single_thread"] = {"value": ks * p["T"] * n1 / el1, "unit": UNIT, "cores": 1,
+                            "kind": "oracle",
+                            "sample": f"{n1} oracle step(s) of {ks} of the {p['K']} samples of "
+                                      f"{p['name']} on one thread, {el1:.1f} s"}
+    return out
+
+
+def _err_sigma(u_gpu, u_ref, sigma):
+    sig = np.maximum(np.asarray(sigma, np.float64), 1e-30)
+    d = np.abs(np.asarray(u_gpu, np.float64).reshape(-1, len(sig)) -
+               np.asarray(u_ref, np.float64).reshape(-1, len(sig)))
+    return float(np.max(d / sig[None, :]))
+
+
+def _crash_jump(p):
+    """The cost one crash decision adds (quadrotor with spheres), else None."""
+    if p["cost_kind"] != W.COST_QUAD_OBSTACLES:
+        return None
+    base = 2 * p["nx"] + p["nu"] + 1
+    return float(p["cost_params"][base + 1]) if p["cost_params"][base] > 0 else None
+
+
+def _cost_rel(S_gpu, S_ref, p=None):
+    """max |dS| / max(1, |S|) over the samples, with whole crash-cost jumps (a
+    step decided the other way within FP32 rounding of a sphere's surface)
+    taken out and counted; returns (max relative error, samples with a jump)."""
+    a, b = np.asarray(S_gpu, np.float64), np.asarray(S_ref, np.float64)
+    fin = np.isfinite(a) & np.isfinite(b)
+    if not fin.any():
+        return 0.0, 0
+    d = a[fin] - b[fin]
+    jump = _crash_jump(p) if p is not None else None
+    flips = 0
+    if jump:
+        n = np.rint(d / jump)
+        flips = int(np.count_nonzero(n))
+        d = d - n * jump
+    return float(np.max(np.abs(d) / np.maximum(1.0, np.abs(b[fin])))), flips
+
+
+def oracle_errors(probes):
+    """The oracle leg: each benchmarked form's GPU result (one step on the
+    bench inputs, run outside every timed region) against the FP64 oracle on
+    the same seeded inputs.  u_new errors are max |du| / sigma over (t, j);
+    cost errors max |dS| / max(1, |S|) over the samples; the gradient error is
+    max |dg| / max |g|.  'cost_propagated' is |u(S_gpu) - u(S_oracle)| / sigma
+    with the oracle's own FP64 weighting and update: the part of the u_new
+    difference that FP32 cost resolution accounts for.  Crash decisions taken
+    the other way (a step within FP32 rounding of a sphere's surface) are
+    counted and their whole cost jumps left out of cost_max_rel."""
+    import oracle
+    nt = os.cpu_count() or 1
+    out = {}
+    for name, pr in probes.items():
+        kind = pr["kind"]
+        if kind == "step":
+            p = pr["problem"]
+            o = oracle.mppi_step(p, step=pr["step"], n_threads=nt, want_eps=True)
+            wg, _, cg = oracle.weights(pr["costs"], p["lam"])
+            prop = 0.0
+            if cg == 0 and o["status"] == 0:
+                prop = _err_sigma(np.einsum("k,ktj->tj", wg - o["w"], o["eps"]),
+                                  np.zeros((p["T"], p["nu"])), p["sigma"])
+            crel, flips = _cost_rel(pr["costs"], o["S"], p)
+            out[name] = {"u_new_err_over_sigma": _err_sigma(pr["u_new"], o["u_new"], p["sigma"]),
+                         "cost_max_rel": crel, "crash_decisions_flipped": flips,
+                         "cost_propagated_over_sigma": prop,
+                         "ess": float(o["stats"][3])}
+        elif kind == "batched":
+            errs, props, crel, flips = [], [], 0.0, 0
+            for p, (u_g, S_g) in zip(pr["problems"], pr["outputs"]):
+                o = oracle.mppi_step(p, n_threads=nt, want_eps=True)
+                wg, _, _ = oracle.weights(S_g, p["lam"])
+                errs.append(_err_sigma(u_g, o["u_new"], p["sigma"]))
+                props.append(_err_sigma(np.einsum("k,ktj->tj", wg - o["w"], o["eps"]),
+                                        np.zeros((p["T"], p["nu"])), p["sigma"]))
+                c, f = _cost_rel(S_g, o["S"], p)
+                crel, flips = max(crel, c), flips + f
+            errs, props = np.array(errs), np.array(props)
+            over = errs > 1e-4
+            out[name] = {"u_new_err_over_sigma_max": float(errs.max()),
+                         "u_new_err_over_sigma_median": float(np.median(errs)),
+                         "instances": int(len(errs)),
+                         "instances_above_1e-4_sigma": int(over.sum()),
+                         "above_explained_by_cost_propagation": bool(
+                             np.all(np.abs(errs[over] - props[over]) <= 1e-5)),
+                         "cost_max_rel": crel, "crash_decisions_flipped": flips}
+        elif kind == "iterate":
+            p = pr["problem"]
+            o = oracle.mppi_iterate(p, pr["rounds"], pr["gamma"], n_threads=nt)
+            out[name] = {"u_new_err_over_sigma": _err_sigma(pr["u_new"], o["u_new"], p["sigma"])}
+        elif kind == "cem":
+            p = pr["problem"]
+            o = oracle.cem_step(p, pr["fraction"], n_threads=nt)
+            out[name] = {"u_new_err_over_sigma": _err_sigma(pr["u_new"], o["u_new"], p["sigma"]),
+                         "elite_set_equal": bool(np.array_equal(np.flatnonzero(pr["weights"]),
+                                                                np.flatnonzero(o["w"])))}
+        elif kind == "grad":
+            p = pr["problem"]
+            g_o, st = oracle.mppi_grad_cartpole(p, pr["G"], n_threads=nt)
+            o = oracle.mppi_step(p, n_threads=nt)
+            g_g = np.asarray(pr["grad"], np.float64)
+            out[name] = {"grad_rel_err": float(np.max(np.abs(g_g - g_o)) / np.max(np.abs(g_o))),
+                         "u_new_err_over_sigma": _err_sigma(pr["u_new"], o["u_new"], p["sigma"])}
+    return out
 
 
 def reference_arm(args, p):
@@ -291,6 +416,46 @@ def time_steps_flushed(fn, steps, flush, warmup=3):
     return sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps
 
 
+def step_times_flushed(fn, steps, flush, warmup=3):
+    """Per-call milliseconds of fn() with the L2 flushed before each call."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        fn()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def graph_replay_latency(ctl, x0, u_nom, u_new, stats, flush, steps=1000, warmup=50):
+    """mppi_step captured once in a CUDA graph, then replayed: CUDA events
+    around each of `steps` replays after `warmup` untimed ones, L2 flushed
+    before each.  Returns p50 / p99 / mean in ms."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        ctl.step_into(x0, u_nom, u_new, stats=stats)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ctl.step_into(x0, u_nom, u_new, stats=stats)
+    torch.cuda.synchronize()
+    t = step_times_flushed(g.replay, steps, flush, warmup=warmup)
+    del g
+    return {"steps": steps, "warmup": warmup, "p50_ms": float(np.percentile(t, 50)),
+            "p99_ms": float(np.percentile(t, 99)), "mean_ms": float(np.mean(t)),
+            "l2": "flushed before every replay"}
+
+
 def extensions(m, dev, peak_tflops, bf16_peak):
     """The batched, differentiable, multi-iteration, CEM and BF16-MLP forms, and
     the paper's own diff-drive benchmark over its K sweep, on the
@@ -299,6 +464,42 @@ def extensions(m, dev, peak_tflops, bf16_peak):
     import torch
     out = {}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # configuration 0: cart-pole K=1024, T=100 (latency-bound: 100 dependent steps)
+    p = W.cartpole()
+    ctl = m.MPPI.from_problem(p)
+    x0 = torch.tensor(p["x0"], dtype=torch.float32, device=dev)
+    u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device=dev)
+    un = torch.empty_like(u)
+    st = torch.empty(4, dtype=torch.float32, device=dev)
+    t = step_times_flushed(lambda: ctl.step_into(x0, u, un, stats=st), 200, flush)
+    ms0 = float(np.mean(t))
+    ctl.profile(True)
+    for i in range(50):
+        flush.fill_(float(i))
+        ctl.step_into(x0, u, un, stats=st)
+    torch.cuda.synchronize()
+    prof = ctl.profile_read()
+    ctl.profile(False)
+    roll_ms = prof["rollout"][0] / max(prof["rollout"][1], 1)
+    tf0 = FLOPS_PER_ROLLOUT_STEP["cartpole"] * p["K"] * p["T"] / (roll_ms * 1e-3) / 1e12
+    x0_h = torch.tensor(p["x0"], dtype=torch.float32).pin_memory()
+    u_h = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32).pin_memory()
+    un_h = torch.empty_like(u_h).pin_memory()
+    st_h = torch.empty(4, dtype=torch.float32).pin_memory()
+    for _ in range(3):
+        ctl.step_host_ptr(x0_h.data_ptr(), u_h.data_ptr(), un_h.data_ptr(), st_h.data_ptr())
+    t0 = time.perf_counter()
+    for _ in range(200):
+        ctl.step_host_ptr(x0_h.data_ptr(), u_h.data_ptr(), un_h.data_ptr(), st_h.data_ptr())
+    e2e0 = (time.perf_counter() - t0) * 1e3 / 200
+    out["cartpole"] = {"workload": "cart-pole K=1024 T=100 (configuration 0)",
+                       "ms_per_step": ms0, "rollout_steps_per_s": p["K"] * p["T"] / (ms0 * 1e-3),
+                       "latency_ms": {"p50": float(np.percentile(t, 50)),
+                                      "p99": float(np.percentile(t, 99))},
+                       "e2e_ms_per_step": e2e0, "rollout_kernel_ms": roll_ms,
+                       "achieved_tflops": tf0, "fp32_roofline_frac": tf0 / peak_tflops,
+                       "graph_replay": graph_replay_latency(ctl, x0, u, un, st, flush)}
+    ctl.close()
     # batched: 256 instances, cart-pole and quadrotor, uneven K and T
     probs = W.batched()
     b = m.MPPIBatch(probs)
@@ -438,6 +639,99 @@ def extensions(m, dev, peak_tflops, bf16_peak):
     return out
 
 
+def _f32_inputs(p):
+    """The problem with its inputs rounded to FP32, as the GPU receives them,
+    so that the oracle starts from the same values."""
+    q = dict(p)
+    for key in ("dyn_params", "cost_params", "sigma", "x0", "u_nom", "map", "u_target"):
+        if q.get(key) is not None:
+            q[key] = np.asarray(q[key], dtype=np.float32).astype(np.float64)
+    q["dt"] = float(np.float32(p["dt"]))
+    q["lam"] = float(np.float32(p["lam"]))
+    return q
+
+
+def parity_probes(m, dev):
+    """One untimed step of every benchmarked form on its bench inputs, with the
+    step counter at 0, read back to the host for the oracle leg."""
+    import torch
+
+    def one_step(p, **kw):
+        ctl = m.MPPI.from_problem(p, **kw)
+        x0 = torch.tensor(p["x0"], dtype=torch.float32, device=dev)
+        u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device=dev)
+        return ctl, x0, u
+
+    probes = {}
+    for name, p, kw in (("quadrotor", W.quadrotor(), {}), ("cartpole", W.cartpole(), {}),
+                        ("bicycle_fp32", W.bicycle_mlp(), {}),
+                        ("bicycle_bf16", W.bicycle_mlp(), {"precision": m.MPPI_PREC_BF16_MLP}),
+                        ("diffdrive", W.diff_drive(), {})):
+        p = _f32_inputs(p)
+        ctl, x0, u = one_step(p, **kw)
+        r = ctl.step(x0, u, want_weights=True, want_costs=True)
+        torch.cuda.synchronize()
+        probes[name] = {"kind": "step", "problem": p, "step": 0,
+                        "u_new": r["u_new"].cpu().numpy(), "costs": r["costs"].cpu().numpy()}
+        ctl.close()
+    # batched: every instance
+    probs = [_f32_inputs(p) for p in W.batched()]
+    b = m.MPPIBatch(probs)
+    b.step()
+    torch.cuda.synchronize()
+    probes["batched"] = {"kind": "batched", "problems": probs,
+                         "outputs": [(b.u_new_of(i).cpu().numpy(),
+                                      b.samples_of(i)[0].cpu().numpy()) for i in range(len(probs))]}
+    b.close()
+    # rounds with the DMD-MPC step size, and CEM, on the headline workload
+    p = _f32_inputs(W.quadrotor())
+    ctl, x0, u = one_step(p)
+    ctl.set_iterations(3, 0.5)
+    r = ctl.step(x0, u)
+    torch.cuda.synchronize()
+    probes["multi_iteration"] = {"kind": "iterate", "problem": p, "rounds": 3, "gamma": 0.5,
+                                 "u_new": r["u_new"].cpu().numpy()}
+    ctl.close()
+    ctl, x0, u = one_step(p)
+    ctl.set_cem(0.1)
+    r = ctl.step(x0, u, want_weights=True)
+    torch.cuda.synchronize()
+    probes["cem"] = {"kind": "cem", "problem": p, "fraction": float(np.float32(0.1)),
+                     "u_new": r["u_new"].cpu().numpy(), "weights": r["weights"].cpu().numpy()}
+    ctl.close()
+    # differentiable: the adjoint gradient of sum(G u_new), G = dL/du_new
+    p = _f32_inputs(W.differentiable())
+    ctl, x0, u = one_step(p)
+    r = ctl.step(x0, u)
+    G = 2.0 * (r["u_new"].reshape(-1) - torch.tensor(p["u_target"].reshape(-1),
+                                                     dtype=torch.float32, device=dev))
+    grad = ctl.backward(G)
+    torch.cuda.synchronize()
+    probes["differentiable"] = {"kind": "grad", "problem": p,
+                                "G": G.cpu().numpy().astype(np.float64).reshape(p["T"], 1),
+                                "grad": grad.cpu().numpy(), "u_new": r["u_new"].cpu().numpy()}
+    ctl.close()
+    return probes
+
+
+def fp32_peak(m):
+    """The FP32 pipe peak: measured by the library's FMA probe (scalar and
+    paired FMA, the faster of the two) and derived from the SM count and the
+    maximum SM clock."""
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
+    derived = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    meas = {}
+    for name, pair in (("scalar_fma", False), ("f32x2_fma", True)):
+        m.fp32_fma_probe(pair, 20000)                    # settle the clock
+        tf, ms = m.fp32_fma_probe(pair, 400000)
+        meas[name] = {"tflops": tf, "ms": ms}
+    best = max(v["tflops"] for v in meas.values())
+    return {"measured_tflops": best, "derived_tflops": derived, "probe": meas,
+            "sms": props.multi_processor_count, "sm_max_mhz": sm_max}
+
+
 def workload_config(p):
     return {"workload": f"{p['name']} (lambda={p['lam']}, seeded inputs)",
             "K": p["K"], "T": p["T"], "nx": p["nx"], "nu": p["nu"],
@@ -546,10 +840,13 @@ def main():
     h2d = (p["nx"] + p["T"] * p["nu"]) * 4
     d2h = (p["T"] * p["nu"] + 4) * 4
 
+    # ---- graph-replayed latency of the same step -------------------------------
+    graph = graph_replay_latency(ctl, x0, u_nom, u_new, stats, flush)
+
     # ---- roofline of the rollout kernel ---------------------------------------
     props = torch.cuda.get_device_properties(dev)
-    sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
-    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peak = fp32_peak(m)
+    peak_tflops = peak["measured_tflops"]
     roll_ms, roll_n = prof["rollout"]
     upd_ms, upd_n = prof["update"]
     roll_avg_ms = roll_ms / max(roll_n, 1)
@@ -568,8 +865,11 @@ def main():
                 "kernel_ms": roll_avg_ms, "update_kernel_ms": upd_ms / max(upd_n, 1),
                 "peak_note": ("measured BF16 GEMM burst (MEASURED_PEAKS.json), MLP flops only"
                               if args.precision == "bf16" else
-                              f"FP32 pipe: {props.multi_processor_count} SMs x 128 lanes x 2 "
-                              f"x {sm_max:.0f} MHz (max SM clock)")}
+                              "of measured: FP32 FMA rate from the library's probe "
+                              "(mppi_fp32_fma_probe, the faster of scalar and f32x2 FMA chains "
+                              f"on all SMs); derived {peak['derived_tflops']:.1f} TFLOP/s = "
+                              f"{peak['sms']} SMs x 128 lanes x 2 x {peak['sm_max_mhz']:.0f} MHz"),
+                "fp32_peak": peak}
     traffic_file = os.path.join(ROOT, "profiles", f"rollout_{args.workload}_traffic.json")
     if args.precision == "bf16":
         traffic_file = os.path.join(ROOT, "profiles", "rollout_bicycle_bf16_traffic.json")
@@ -597,11 +897,27 @@ def main():
         "gpu_launches": roll_n + upd_n,
         "roofline": roofline,
         "clocks": clk,
+        "graph_replay": graph,
     }
     if world == 1 and not args.no_extensions and args.workload == "quadrotor":
-        line["extensions"] = extensions(m, dev, peak_tflops, measured_peaks().get("bf16_tflops"))
+        line["extensions"] = extensions(m, dev, peak["measured_tflops"],
+                                        measured_peaks().get("bf16_tflops"))
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
+        if args.workload == "quadrotor" and args.K is None:
+            # the oracle leg: every form's GPU result against the FP64 oracle
+            errs = oracle_errors(parity_probes(m, dev))
+            line["oracle_err"] = errs["quadrotor"]
+            for name, key in (("cartpole", "cartpole"), ("batched", "batched"),
+                              ("differentiable", "differentiable"),
+                              ("multi_iteration", "multi_iteration"), ("cem", "cem")):
+                if "extensions" in line and key in line["extensions"]:
+                    line["extensions"][key]["oracle_err"] = errs[name]
+            if "extensions" in line:
+                line["extensions"]["bf16_mlp"]["oracle_err"] = {
+                    "bf16": errs["bicycle_bf16"], "fp32": errs["bicycle_fp32"]}
+                line["extensions"]["diffdrive_sweep"]["oracle_err_K16384"] = errs["diffdrive"]
+            line["oracle_err_all"] = errs
     print(json.dumps(line), flush=True)
     ctl.close()
     if world > 1:

@@ -361,6 +361,15 @@ MPPI_API mppi_status mppi_batch_samples(const mppi_batch *b, int i, float *costs
                                         float *weights_d, void *cuda_stream);
 MPPI_API void mppi_batch_destroy(mppi_batch *b);
 
+/* Diagnostic (no paper counterpart): the FP32 FMA rate of the current
+ * device, the denominator of the rollout kernels' roofline.  Runs independent
+ * FMA chains on every SM (pair = 0: scalar fmaf; pair = 1: the paired f32x2
+ * FMA), `iters` iterations per chain, synchronously on the legacy stream after
+ * one warm-up launch; *ms_out = the timed launch's duration (CUDA events) and
+ * *flops_out = its FP32 operations (FMA = 2).  Errors: MPPI_ERR_INVALID_ARG
+ * (iters outside [1, 2^24], pair not 0/1, NULL outputs), MPPI_ERR_CUDA. */
+MPPI_API mppi_status mppi_fp32_fma_probe(int pair, int iters, float *ms_out, double *flops_out);
+
 /* ---------------------------------------------------------------------------
  * Allocation-free weighting and update.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory, such as
@@ -380,10 +389,12 @@ MPPI_API void mppi_batch_destroy(mppi_batch *b);
  * T * nu <= MPPI_NOALLOC_MAX_TNU, 1 <= nu <= 4; larger requests return
  * MPPI_ERR_INVALID_ARG without touching the GPU.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
- * the array and it keeps the last call's contents (the counters that must
- * start at zero are cleared by each call), so calls that overlap on the GPU
- * race: order them on one stream. */
+ * current; make that first call before any stream capture.  That address is
+ * kept for the life of the process: do not reset the device (cudaDeviceReset)
+ * after the first call, since later calls would use the old address.  All
+ * calls share the array and it keeps the last call's contents (the counters
+ * that must start at zero are cleared by each call), so calls that overlap on
+ * the GPU race: order them on one stream. */
 #define MPPI_NOALLOC_MAX_K 65536
 #define MPPI_NOALLOC_MAX_TNU 4096
 MPPI_API mppi_status mppi_update_noalloc(const float *costs_d, int K, int T, int nu, float lambda,

@@ -19,7 +19,7 @@ from ._lib import (MPPIError, CostDesc, DynamicsDesc, Options, check, load,  # n
                    MPPI_PREC_FP32, MPPI_PREC_BF16_MLP)
 
 __all__ = ["build", "MPPI", "MPPIError", "MPPIStep", "mppi_sample_noise",
-           "mppi_update_noalloc", "library_path"]
+           "mppi_update_noalloc", "fp32_fma_probe", "library_path"]
 
 library_path = _build.LIB_PATH
 
@@ -270,6 +270,17 @@ def mppi_sample_noise(seed, step, K, Q, bits=None, z=None, stream=None):
     st = L.mppi_sample_noise(int(seed) & (2**64 - 1), int(step) & (2**64 - 1), int(K), int(Q),
                              _dptr(bits), _dptr(z), _stream_handle(stream))
     check(st, "mppi_sample_noise")
+
+
+def fp32_fma_probe(pair=False, iters=200000):
+    """Measured FP32 FMA rate of the current device (``mppi_fp32_fma_probe``):
+    returns (TFLOP/s, milliseconds of the timed launch)."""
+    L = load()
+    ms = ctypes.c_float()
+    fl = ctypes.c_double()
+    check(L.mppi_fp32_fma_probe(1 if pair else 0, int(iters), ctypes.byref(ms), ctypes.byref(fl)),
+          "mppi_fp32_fma_probe")
+    return fl.value / (ms.value * 1e-3) / 1e12, ms.value
 
 
 NOALLOC_MAX_K = 65536

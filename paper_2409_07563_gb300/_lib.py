@@ -111,6 +111,10 @@ def _optional(L):
         L.mppi_update_noalloc.argtypes = [vp, i, i, i, ctypes.c_float, c_float_p, u64, u64,
                                           vp, vp, vp, vp, vp]
         L.mppi_update_noalloc.restype = ctypes.c_int
+    if hasattr(L, "mppi_fp32_fma_probe"):
+        L.mppi_fp32_fma_probe.argtypes = [i, i, ctypes.POINTER(ctypes.c_float),
+                                          ctypes.POINTER(ctypes.c_double)]
+        L.mppi_fp32_fma_probe.restype = ctypes.c_int
     if hasattr(L, "mppi_batch_create"):
         L.mppi_batch_create.argtypes = [i, ctypes.POINTER(InstanceDesc), ctypes.POINTER(Options),
                                         ctypes.POINTER(vp)]

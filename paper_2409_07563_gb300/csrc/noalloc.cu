@@ -181,7 +181,9 @@ __global__ void __launch_bounds__(kNaThreads) na_update_kernel(const NaParams p,
 }
 
 // Device address of the scratch array, looked up once per device with that
-// device current (the array's host-side name is only a stand-in).
+// device current (the array's host-side name is only a stand-in).  It is kept
+// for the life of the process, so a device reset after the first call is not
+// supported (the cached address would belong to the destroyed context).
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 float *g_scratch_ptr[kMaxDevices] = {};

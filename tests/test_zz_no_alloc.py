@@ -6,12 +6,15 @@ takes the caller's sample costs and runs the weighting and update with a
 fixed scratch array inside the library.  Here it is given the costs that
 mppi_step produced and must reproduce mppi_step's weights, statistics and
 u_new within the stage tolerances of the parity tests, on two calls in a row
-(consecutive steps, so the shared scratch is reused).  The file is named to
-be collected last.
+(consecutive steps, so the shared scratch is reused).  Hand-made costs with
++inf and NaN, and costs that are all non-finite, are checked against the
+oracle's weighting and the closed-form fallback (u_new = u_nom).  The file is
+named to be collected last.
 """
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
 from _util import as_f32_problem
 
@@ -83,3 +86,56 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(m):
                                1.0, sig, 0, 0, ctypes.c_void_p(u.data_ptr()),
                                ctypes.c_void_p(u.data_ptr()), None, None, None)
     assert st == 1
+
+
+def test_noalloc_non_finite_costs_against_the_oracle(m):
+    """+inf and NaN costs get weight 0 (the oracle's weighting of the finite
+    ones); the update is u_nom + sum_k w_k sigma z_k with the oracle's
+    normals."""
+    K, T, nu, lam, seed, step = 1000, 12, 2, 3.0, 99, 5
+    sig = np.array([0.7, 1.3], np.float32).astype(np.float64)
+    rng = np.random.default_rng(3)
+    S = rng.uniform(10.0, 30.0, K).astype(np.float32)
+    S[rng.choice(K, 40, replace=False)] = np.inf
+    S[rng.choice(K, 40, replace=False)] = np.nan
+    u_nom = rng.uniform(-1, 1, (T, nu)).astype(np.float32)
+    costs = torch.tensor(S, device="cuda")
+    u = torch.tensor(u_nom.reshape(-1), device="cuda")
+    u_new = torch.full_like(u, float("nan"))
+    w = torch.full((K,), float("nan"), device="cuda")
+    stats = torch.full((4,), float("nan"), device="cuda")
+    m.mppi_update_noalloc(costs, lam, sig, seed, step, u, u_new, w, stats)
+    torch.cuda.synchronize()
+    w_o, st_o, code = oracle.weights(S.astype(np.float64), lam)
+    assert code == 0
+    g_w = w.cpu().numpy().astype(np.float64)
+    assert np.all(g_w[~np.isfinite(S)] == 0.0)
+    x = (S.astype(np.float64) - st_o[1]) / lam
+    fin = np.isfinite(S)
+    assert np.all(np.abs(g_w[fin] - w_o[fin]) <= 2e-5 * (1 + np.abs(x[fin])) * w_o[fin] + 1e-9)
+    g_s = stats.cpu().numpy().astype(np.float64)
+    assert g_s[1] == st_o[1]
+    assert g_s[2] == pytest.approx(st_o[2], rel=2e-5)
+    assert g_s[3] == pytest.approx(st_o[3], rel=1e-4)
+    z = oracle.normals(seed, step, K, T, nu)
+    u_ref = u_nom.astype(np.float64) + np.einsum("k,ktj->tj", w_o, sig[None, None, :] * z)
+    g_u = u_new.cpu().numpy().astype(np.float64).reshape(T, nu)
+    assert np.all(np.abs(g_u - u_ref) <= 1e-5 * sig[None, :])
+
+
+def test_noalloc_all_costs_non_finite_returns_the_nominal(m):
+    K, T, nu = 300, 9, 1
+    S = np.full(K, np.inf, np.float32)
+    S[::3] = np.nan
+    u_nom = np.linspace(-1, 1, T * nu).astype(np.float32)
+    costs = torch.tensor(S, device="cuda")
+    u = torch.tensor(u_nom, device="cuda")
+    u_new = torch.full_like(u, float("nan"))
+    w = torch.full((K,), float("nan"), device="cuda")
+    stats = torch.full((4,), float("nan"), device="cuda")
+    m.mppi_update_noalloc(costs, 1.0, [1.0], 7, 0, u, u_new, w, stats)
+    torch.cuda.synchronize()
+    assert np.array_equal(u_new.cpu().numpy(), u_nom)
+    assert np.all(w.cpu().numpy() == 0.0)
+    g_s = stats.cpu().numpy()
+    assert np.isinf(g_s[0]) and np.isinf(g_s[1]) and g_s[2] == 0.0 and g_s[3] == 0.0
