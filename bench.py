@@ -620,9 +620,19 @@ def extensions(m, dev, peak_tflops, bf16_peak):
     u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device=dev)
     un = torch.empty_like(u)
     res = {}
-    for name, prec in (("bf16", m.MPPI_PREC_BF16_MLP), ("fp32", m.MPPI_PREC_FP32)):
-        c = m.MPPI.from_problem(p, precision=prec)
-        res[name] = time_steps_flushed(lambda: c.step_into(x0, u, un), 10, flush)
+    for name, prec, var in (("bf16", m.MPPI_PREC_BF16_MLP, 0), ("fp32", m.MPPI_PREC_FP32, 0),
+                            ("bf16_tcgen05", m.MPPI_PREC_BF16_MLP, 2)):
+        c = m.MPPI.from_problem(p, precision=prec, rollout_variant=var)
+        res[name] = time_steps_flushed(lambda: c.step_into(x0, u, un), 20, flush)
+        if name in ("bf16", "bf16_tcgen05"):
+            c.profile(True)
+            for i in range(20):
+                flush.fill_(float(i))
+                c.step_into(x0, u, un)
+            torch.cuda.synchronize()
+            prof = c.profile_read()
+            c.profile(False)
+            res[name + "_rollout_kernel"] = prof["rollout"][0] / max(prof["rollout"][1], 1)
         c.close()
     mlp_tflops = 2 * (6 * 64 + 64 * 64 + 64 * 4) * p["K"] * p["T"] / (res["bf16"] * 1e-3) / 1e12
     # the 128 hidden-layer tanh per rollout-step run on the XU (MUFU) pipe:
@@ -630,8 +640,24 @@ def extensions(m, dev, peak_tflops, bf16_peak):
     props = torch.cuda.get_device_properties(dev)
     xu_peak = props.multi_processor_count * 16 * measured_peaks().get("sm_max_mhz", 2070.0) * 1e6
     tanh_rate = 128 * p["K"] * p["T"] / (res["bf16"] * 1e-3)
+    mlp_flops = 2 * (6 * 64 + 64 * 64 + 64 * 4) * p["K"] * p["T"]
+    kmlp = mlp_flops / (res["bf16_rollout_kernel"] * 1e-3) / 1e12
+    kmlp_tc = mlp_flops / (res["bf16_tcgen05_rollout_kernel"] * 1e-3) / 1e12
     out["bf16_mlp"] = {"workload": "bicycle + MLP 6-64-64-4, K=16384 T=100, costmap 512x512",
+                       "kernel": "bicycle_mlp_bf16_kernel (warp-level mma.sync, weights in "
+                                 "registers; the faster of the two tensor-core kernels here)",
                        "ms_per_step": res["bf16"], "fp32_ms_per_step": res["fp32"],
+                       "rollout_kernel_ms": res["bf16_rollout_kernel"],
+                       "kernel_mlp_tflops": kmlp,
+                       "kernel_bf16_tensor_frac": kmlp / bf16_peak if bf16_peak else None,
+                       "tcgen05": {"kernel": "bicycle_mlp_tc_kernel (tcgen05.mma, FP32 "
+                                             "accumulators in tensor memory, two 64-sample "
+                                             "tiles per CTA)",
+                                   "ms_per_step": res["bf16_tcgen05"],
+                                   "rollout_kernel_ms": res["bf16_tcgen05_rollout_kernel"],
+                                   "kernel_mlp_tflops": kmlp_tc,
+                                   "kernel_bf16_tensor_frac":
+                                       kmlp_tc / bf16_peak if bf16_peak else None},
                        "rollout_steps_per_s": p["K"] * p["T"] / (res["bf16"] * 1e-3),
                        "mlp_tflops": mlp_tflops,
                        "bf16_tensor_frac": mlp_tflops / bf16_peak if bf16_peak else None,
@@ -752,6 +778,8 @@ def main():
                     help="quadrotor (configuration 1, the headline) or a diagnostic run")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
                     help="bf16: the bicycle workload's MLP on the tensor cores (diagnostic)")
+    ap.add_argument("--rollout-variant", type=int, default=0,
+                    help="the context's rollout_variant option (diagnostic)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -773,7 +801,8 @@ def main():
     import paper_2409_07563_gb300 as m
     m.build()
     ctl = m.MPPI.from_problem(
-        p, precision=m.MPPI_PREC_BF16_MLP if args.precision == "bf16" else m.MPPI_PREC_FP32)
+        p, precision=m.MPPI_PREC_BF16_MLP if args.precision == "bf16" else m.MPPI_PREC_FP32,
+        rollout_variant=args.rollout_variant)
     x0 = torch.tensor(p["x0"], dtype=torch.float32, device=dev)
     u_nom = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device=dev)
     u_new = torch.empty_like(u_nom)
@@ -857,7 +886,9 @@ def main():
         mlp = 2 * (6 * 64 + 64 * 64 + 64 * 4) * rollout_steps / (roll_avg_ms * 1e-3) / 1e12
         bf16_peak = measured_peaks().get("bf16_tflops", 1979.2)
         achieved, peak_tflops = mlp, bf16_peak
-        kernel_name = "bicycle_mlp_bf16_kernel (MLP on mma.sync BF16, FP32 accumulate)"
+        kernel_name = ("bicycle_mlp_tc_kernel (MLP on tcgen05.mma BF16, FP32 accumulators in "
+                       "tensor memory)" if args.rollout_variant == 2 else
+                       "bicycle_mlp_bf16_kernel (MLP on mma.sync BF16, FP32 accumulate)")
     roofline = {"bound": "tensor" if args.precision == "bf16" else "alu",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,

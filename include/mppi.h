@@ -170,7 +170,11 @@ typedef struct {
                                  32 obstacles).  BICYCLE_MLP with COSTMAP_SPEED at
                                  FP32: 0 takes four lanes per two samples (the
                                  MLP's hidden units split over the lanes), 1 one
-                                 sample per thread.  The other models: 0 takes a
+                                 sample per thread.  BICYCLE_MLP at BF16_MLP: 0 (or
+                                 1) the warp-level mma.sync kernel, 2 the tcgen05
+                                 kernel (two 64-sample tiles per CTA, accumulators
+                                 in tensor memory, block_threads 0).  The other
+                                 models: 0 takes a
                                  dynamics warp, a noise warp and a cost warp per 32
                                  samples (block_threads 96 or 192, else one sample
                                  per thread), 1 one sample per thread */

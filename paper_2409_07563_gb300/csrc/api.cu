@@ -113,11 +113,18 @@ void plan_launch(mppi_ctx &c) {
     const bool split = quad && !pair1 && asked != mppi::kVariantQuadGroup &&
                        c.block_threads % 64 == 0;
     const bool group = quad && !pair1 && !split;
-    const bool mlp_tc = c.precision == MPPI_PREC_BF16_MLP;
+    const bool bf16 = c.precision == MPPI_PREC_BF16_MLP;
+    // BF16 MLP: the warp-level mma.sync kernel by default (measured on GB300
+    // at K = 16384, T = 100: 116 us against 198 for the tcgen05 kernel, whose
+    // three dependent layers per step each wait for an MMA round trip);
+    // rollout_variant 2 selects the tcgen05 kernel
+    const bool mlp_tc = bf16 && c.variant_opt == mppi::kVariantQuadGroup;
+    const bool mlp_sync = bf16 && !mlp_tc;
     const bool mlp32 = mppi::mlp_f32_applicable(c) && c.variant_opt != mppi::kVariantGeneric;
-    const bool gpair = !mlp_tc && c.variant_opt == 0 && mppi::pair_rollout_applicable(c) &&
+    const bool gpair = !bf16 && c.variant_opt == 0 && mppi::pair_rollout_applicable(c) &&
                        c.block_threads % 96 == 0 && c.block_threads <= 192;
-    pl.variant = mlp_tc  ? mppi::kVariantMlpBf16
+    pl.variant = mlp_tc    ? mppi::kVariantMlpTc
+                 : mlp_sync ? mppi::kVariantMlpBf16
                  : mlp32 ? mppi::kVariantMlpF32
                  : gpair ? mppi::kVariantGenericPair
                  : pair1 ? mppi::kVariantQuadPair
@@ -125,11 +132,14 @@ void plan_launch(mppi_ctx &c) {
                  : group ? mppi::kVariantQuadGroup
                          : mppi::kVariantGeneric;
     // threads per sample (the FP32 MLP: four lanes per two samples)
-    const int lanes = mlp_tc || mlp32 ? 2 : gpair ? 3 : split ? 8 : pair1 ? roles : group ? 4 : 1;
+    const int lanes = mlp_tc ? 3 : mlp_sync || mlp32 ? 2 : gpair ? 3 : split ? 8 : pair1 ? roles
+                      : group ? 4 : 1;
     const long threads_needed = static_cast<long>(c.K) * lanes;
-    if (c.block_threads > 0) {
+    if (mlp_tc) {
+        pl.rollout_threads = 384;  // two 64-sample tiles: 2 x 4 tile warps, four cost warps
+    } else if (c.block_threads > 0) {
         pl.rollout_threads = c.block_threads;
-    } else if (mlp_tc) {
+    } else if (mlp_sync) {
         // warp pairs of 32 samples spread over every SM first, at most four
         // per block: a block's warps occupy consecutive warp slots, so four
         // pairs put one dynamics warp on each SM sub-partition (measured on
@@ -314,7 +324,12 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     if (o.rollout_variant == 3 && o.block_threads % 64 != 0) return MPPI_ERR_INVALID_ARG;
     if (o.rollout_variant == 4 && o.block_threads % 128 != 0) return MPPI_ERR_INVALID_ARG;
     if (o.precision == MPPI_PREC_BF16_MLP && o.block_threads % 64 != 0) return MPPI_ERR_INVALID_ARG;
-    if (o.rollout_variant >= 2 &&
+    // the tcgen05 MLP kernel (rollout_variant 2) has one shape (384 threads per
+    // 128 samples)
+    const bool bf16_tc = o.precision == MPPI_PREC_BF16_MLP && o.rollout_variant == 2;
+    if (bf16_tc && o.block_threads != 0) return MPPI_ERR_INVALID_ARG;
+    if (o.precision == MPPI_PREC_BF16_MLP && o.rollout_variant > 2) return MPPI_ERR_UNSUPPORTED;
+    if (o.rollout_variant >= 2 && !bf16_tc &&
         (dyn->kind != MPPI_DYN_QUADROTOR ||
          (cost->kind == MPPI_COST_QUAD_OBSTACLES && cost->n_params > 33 + 4 * 32)))
         return MPPI_ERR_UNSUPPORTED;
@@ -412,6 +427,7 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
         : c->plan.variant == mppi::kVariantQuadSplit ? mppi::quad_split_smem_bytes(*c, c->plan.rollout_threads)
         : c->plan.variant == mppi::kVariantQuadPair ? mppi::quad_pair_smem_bytes(*c, c->plan.rollout_threads)
         : c->plan.variant == mppi::kVariantMlpBf16 ? mppi::mlp_bf16_smem_bytes(*c, c->plan.rollout_threads)
+        : c->plan.variant == mppi::kVariantMlpTc ? mppi::mlp_tc_smem_bytes(*c)
         : c->plan.variant == mppi::kVariantMlpF32 ? mppi::mlp_f32_smem_bytes(*c, c->plan.rollout_threads)
         : c->plan.variant == mppi::kVariantGenericPair ? mppi::pair_rollout_smem_bytes(*c, c->plan.rollout_threads)
                                                    : mppi::rollout_smem_bytes(*c);
@@ -426,6 +442,7 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
         (c->plan.variant == mppi::kVariantQuadSplit && (e = mppi::quad_split_prepare(*c)) != cudaSuccess) ||
         (c->plan.variant == mppi::kVariantQuadPair && (e = mppi::quad_pair_prepare(*c)) != cudaSuccess) ||
         (c->plan.variant == mppi::kVariantMlpBf16 && (e = mppi::mlp_bf16_prepare(*c)) != cudaSuccess) ||
+        (c->plan.variant == mppi::kVariantMlpTc && (e = mppi::mlp_tc_prepare(*c)) != cudaSuccess) ||
         (c->plan.variant == mppi::kVariantMlpF32 && (e = mppi::mlp_f32_prepare(*c)) != cudaSuccess) ||
         (c->plan.variant == mppi::kVariantGenericPair && (e = mppi::pair_rollout_prepare(*c)) != cudaSuccess)) {
         free_ctx(c);
@@ -472,6 +489,7 @@ mppi_status mppi_step(mppi_ctx *ctx, const float *x0_d, const float *u_nom_d, fl
                 : ctx->plan.variant == mppi::kVariantQuadSplit ? mppi::launch_quad_split(*ctx, p)
                 : ctx->plan.variant == mppi::kVariantQuadPair ? mppi::launch_quad_pair(*ctx, p)
                 : ctx->plan.variant == mppi::kVariantMlpBf16 ? mppi::launch_mlp_bf16(*ctx, p)
+                : ctx->plan.variant == mppi::kVariantMlpTc ? mppi::launch_mlp_tc(*ctx, p)
                 : ctx->plan.variant == mppi::kVariantMlpF32 ? mppi::launch_mlp_f32(*ctx, p)
                 : ctx->plan.variant == mppi::kVariantGenericPair ? mppi::launch_pair_rollout(*ctx, p)
                                                              : mppi::launch_rollout(*ctx, p);

@@ -72,7 +72,8 @@ enum RolloutVariant {
     kVariantQuadPair = 4,
     kVariantMlpBf16 = 5,
     kVariantMlpF32 = 6,
-    kVariantGenericPair = 7
+    kVariantGenericPair = 7,
+    kVariantMlpTc = 8
 };
 
 struct LaunchPlan {
@@ -167,6 +168,11 @@ size_t quad_pair_smem_bytes(const mppi_ctx &c, int threads);
 cudaError_t quad_pair_prepare(const mppi_ctx &c);
 cudaError_t launch_quad_pair(const mppi_ctx &c, const StepParams &p);
 // rollout_mlp_bf16.cu: bicycle + MLP on the tensor cores
+// rollout_mlp_tc.cu: bicycle + MLP with the MLP on tcgen05 tensor cores
+// (128-sample tiles, accumulators in tensor memory)
+size_t mlp_tc_smem_bytes(const mppi_ctx &c);
+cudaError_t mlp_tc_prepare(const mppi_ctx &c);
+cudaError_t launch_mlp_tc(const mppi_ctx &c, const StepParams &p);
 size_t mlp_bf16_smem_bytes(const mppi_ctx &c, int threads);
 cudaError_t mlp_bf16_prepare(const mppi_ctx &c);
 cudaError_t launch_mlp_bf16(const mppi_ctx &c, const StepParams &p);

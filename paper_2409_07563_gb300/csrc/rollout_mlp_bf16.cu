@@ -12,13 +12,9 @@
 //                    layer 3  mma.m16n8k16  1 x 4 tiles      (N = 4 padded to 8)
 //                  (both halves layer by layer, two independent chains),
 //                  then Euler on the MLP's inputs (v, delta, e1, e2)
-//   cost warp      the noise of both channels (Philox blocks of four steps,
-//                  Box-Muller), v_t = u_t + sigma z_t with the importance
-//                  term; the pose (x, y, yaw) of the kinematic bicycle (FP32,
-//                  accurate sincosf/tanf, Euler) from v and delta before the
-//                  step and the yaw-rate residual -- the pose feeds nothing
-//                  back into the MLP, so it leaves the dynamics warp's chain;
-//                  the costmap (bilinear) and speed cost of x_{t+1}
+//   cost warp      bicycle_cost_warp (bicycle_cost_warp.cuh): the noise, the
+//                  pose of the kinematic bicycle and the costmap and speed
+//                  cost of x_{t+1}
 // They exchange v_t and (v, delta, r_yaw, v') of each step through a double-buffered
 // shared ring of four steps per half and meet at one named barrier per half
 // (bar.sync with the pair's id, 64 threads); both execute the same number of
@@ -32,6 +28,7 @@
 // tile.
 #include <cuda_bf16.h>
 
+#include "bicycle_cost_warp.cuh"
 #include "device_common.cuh"
 #include "models.cuh"
 #include "mppi_internal.h"
@@ -102,13 +99,6 @@ struct WarpTiles {
     uint32_t X[32][4];  // BF16 inputs, 32 rows x 8 columns (16 bytes per row)
     float R[32][8];     // FP32 outputs, 32 rows x 8 columns
 };
-
-constexpr int kMlpH = 4;                     // steps per ring half (one Philox block)
-constexpr int kMlpRing = 2 * kMlpH * kWarp;  // entries per ring: [half][step][lane]
-
-__device__ __forceinline__ void mlp_pair_sync(int id) {
-    asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
-}
 
 // Block = G pairs: warps [0, G) run the MLP and the kinematics, [G, 2G) the
 // noise and the cost; pair j synchronises on named barrier 1 + j.
@@ -258,81 +248,9 @@ __global__ void __launch_bounds__(256) bicycle_mlp_bf16_kernel(const StepParams 
             mlp_pair_sync(bar_id);
         }
     } else {
-        const NoiseKey nk = make_noise_key(p.seed, *p.counter);
-        const CostCtx cc{p.map, p.map_h, p.map_w};
-        const float sig0 = p.sigma[0], sig1 = p.sigma[1], iv0 = p.ivar[0], iv1 = p.ivar[1];
-        const int QT = (T + 3) / 4;
-        CompSum J;
-        // v_t of half hc with the importance term
-        auto controls = [&](int hc) {
-            float2 *vb = ring_v + (hc & 1) * kMlpH * kWarp;
-            const int nc = min(kMlpH, T - hc * kMlpH);
-            float z0[4], z1[4];
-            box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(hc)), z0);
-            box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(QT + hc)), z1);
-#pragma unroll
-            for (int s = 0; s < kMlpH; ++s) {
-                if (s < nc) {
-                    const int t = hc * kMlpH + s;
-                    const float ua = s_u[2 * t], ud = s_u[2 * t + 1];
-                    const float va = ua + sig0 * z0[s], vd = ud + sig1 * z1[s];
-                    vb[s * kWarp + lane] = make_float2(va, vd);
-                    J.add(p.lam_beta *
-                          ((va - 0.5f * ua) * (ua * iv0) + (vd - 0.5f * ud) * (ud * iv1)));
-                }
-            }
-        };
-        const float inv_L = 1.0f / p.dyn_params[0];
-        float px = p.x0[0], py = p.x0[1], yaw = p.x0[2];
-        // pose of x_{t+1} (kinematic bicycle, Euler) from v, delta before the
-        // step and the yaw-rate residual; running cost of x_{t+1}; the
-        // terminal cost on x_T
-        // In phases over the half's four steps so that independent work
-        // overlaps: the four tangents, the serial pose chain, the four
-        // costmap lookups, then the sums in step order.  Steps past T occur
-        // only in the last half; their poses are computed from stale ring
-        // entries (every lookup index is clamped into the map) and never
-        // scored.
-        auto states = [&](int hs) {
-            const float4 *xb = ring_x + (hs & 1) * kMlpH * kWarp;
-            const int nx = min(kMlpH, T - hs * kMlpH);
-            float4 q[kMlpH];
-            float tn[kMlpH], cx[kMlpH], cy[kMlpH], cst[kMlpH];
-#pragma unroll
-            for (int s = 0; s < kMlpH; ++s) q[s] = xb[s * kWarp + lane];  // v, delta, r_yaw, v'
-#pragma unroll
-            for (int s = 0; s < kMlpH; ++s) tn[s] = tanf(q[s].y);
-#pragma unroll
-            for (int s = 0; s < kMlpH; ++s) {
-                float sn, cs;
-                sincosf(yaw, &sn, &cs);
-                const float xd0 = q[s].x * cs, xd1 = q[s].x * sn;
-                const float xd2 = q[s].x * tn[s] * inv_L + q[s].z;
-                px += p.dt * xd0;
-                py += p.dt * xd1;
-                yaw += p.dt * xd2;
-                cx[s] = px;
-                cy[s] = py;
-            }
-#pragma unroll
-            for (int s = 0; s < kMlpH; ++s) {
-                const float y[4] = {cx[s], cy[s], 0.f, q[s].w};  // x, y, (yaw unused), v
-                cst[s] = CostmapSpeedCost::state_cost(y, s_cost, cc);
-            }
-#pragma unroll
-            for (int s = 0; s < kMlpH; ++s)
-                if (s < nx) J.add(hs * kMlpH + s == T - 1 ? cst[s] + cst[s] : cst[s]);
-        };
-        controls(0);
-        mlp_pair_sync(bar_id);
-        for (int hh = 0; hh < nh; ++hh) {
-            if (hh + 1 < nh) controls(hh + 1);
-            if (hh >= 1) states(hh - 1);
-            mlp_pair_sync(bar_id);
-        }
-        states(nh - 1);
+        const float tot = bicycle_cost_warp(p, s_u, s_cost, ring_v, ring_x, k, lane, bar_id);
         if (k < p.K) {
-            S = J.value();
+            S = tot;
             k_out = k;
             p.S[k] = S;
         }

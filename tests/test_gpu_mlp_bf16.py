@@ -1,6 +1,9 @@
 """BF16 tensor-core MLP path (precision MPPI_PREC_BF16_MLP) against the FP64
-oracle.  BF16 operands round the MLP inputs, weights and activations to 8
-significant bits, so this path has no 1e-4 sigma bound; what is checked:
+oracle: the warp-level mma.sync kernel (the default) and the tcgen05 kernel
+(rollout_variant 2: two 64-sample tiles per CTA, accumulators in tensor
+memory).  BF16
+operands round the MLP inputs, weights and activations to 8 significant
+bits, so this path has no 1e-4 sigma bound; what is checked:
 
   * every sample's trajectory cost within 1e-3 relative of the oracle's
     (BF16 rounding, unit roundoff 2^-9, of a residual that moves the state by
@@ -31,8 +34,8 @@ def m():
     return mod
 
 
-def run(m, p, precision):
-    ctl = m.MPPI.from_problem(p, precision=precision)
+def run(m, p, precision, **kw):
+    ctl = m.MPPI.from_problem(p, precision=precision, **kw)
     x0 = torch.tensor(p["x0"], dtype=torch.float32, device="cuda")
     u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device="cuda")
     out = ctl.step(x0, u, want_weights=True, want_costs=True)
@@ -40,13 +43,15 @@ def run(m, p, precision):
     return {k: v.cpu().numpy().astype(np.float64) for k, v in out.items()}
 
 
+# rollout_variant 0: the warp-level mma.sync kernel (the default); 2: tcgen05
+@pytest.mark.parametrize("variant", [0, 2])
 @pytest.mark.parametrize("K,T,lam", [(16384, 100, 1.0), (2001, 21, 5.0), (4096, 100, 100.0)])
-def test_bf16_mlp_costs_and_update(m, K, T, lam):
+def test_bf16_mlp_costs_and_update(m, K, T, lam, variant):
     p = as_f32_problem(W.bicycle_mlp(K=K, T=T, lam=lam))
-    g = run(m, p, m.MPPI_PREC_BF16_MLP)
+    g = run(m, p, m.MPPI_PREC_BF16_MLP, rollout_variant=variant)
     o = oracle.mppi_step(p, n_threads=n_threads(), want_eps=True)
     rel = np.abs(g["costs"] - o["S"]) / np.maximum(1.0, np.abs(o["S"]))
-    print(f"\nBF16 MLP K={K} T={T} lam={lam}: S rel err median {np.median(rel):.2e} "
+    print(f"\nBF16 MLP (variant {variant}) K={K} T={T} lam={lam}: S rel err median {np.median(rel):.2e} "
           f"p99 {np.percentile(rel, 99):.2e} max {rel.max():.2e}")
     check_costs(p, g["costs"], o["S"], bf16=True)
     assert np.median(rel) <= 1e-4
@@ -62,12 +67,39 @@ def test_bf16_mlp_costs_and_update(m, K, T, lam):
         assert err.max() <= 0.05
 
 
-def test_bf16_and_fp32_paths_agree_on_costs(m):
+@pytest.mark.parametrize("variant", [0, 2])
+def test_bf16_and_fp32_paths_agree_on_costs(m, variant):
     p = as_f32_problem(W.bicycle_mlp(K=1024, T=60, lam=10.0))
-    g16 = run(m, p, m.MPPI_PREC_BF16_MLP)
+    g16 = run(m, p, m.MPPI_PREC_BF16_MLP, rollout_variant=variant)
     g32 = run(m, p, m.MPPI_PREC_FP32)
     rel = np.abs(g16["costs"] - g32["costs"]) / np.maximum(1.0, np.abs(g32["costs"]))
     assert rel.max() <= BF16_COST_REL
+
+
+@pytest.mark.parametrize("K,T", [(1, 1), (127, 3), (129, 9), (300, 4), (1000, 37), (40000, 6)])
+def test_bf16_mlp_tcgen05_tiles(m, K, T):
+    """tcgen05 kernel: K below, at and across the 128-sample tile (rows past
+    K computed and discarded), horizons ending inside a ring half, more tiles
+    than SMs; every sample's cost and the update stage."""
+    p = as_f32_problem(W.bicycle_mlp(K=K, T=T, lam=100.0))
+    g = run(m, p, m.MPPI_PREC_BF16_MLP, rollout_variant=2)
+    o = oracle.mppi_step(p, n_threads=n_threads(), want_eps=True)
+    check_costs(p, g["costs"], o["S"], bf16=True)
+    w_ref, st_ref, _ = oracle.weights(g["costs"], 100.0)
+    u_iso = p["u_nom"] + np.einsum("k,ktj->tj", w_ref, o["eps"])
+    assert np.all(np.abs(g["u_new"] - u_iso) <= 1e-5 * p["sigma"][None, :])
+
+
+def test_bf16_mlp_tcgen05_equals_mma_sync_closely(m):
+    """The two tensor-core kernels compute the same BF16 MLP (they differ only
+    in where the biases enter the FP32 sums): their costs agree far inside
+    the BF16 bound."""
+    p = as_f32_problem(W.bicycle_mlp(K=4096, T=50, lam=10.0))
+    a = run(m, p, m.MPPI_PREC_BF16_MLP, rollout_variant=2)
+    b = run(m, p, m.MPPI_PREC_BF16_MLP)
+    rel = np.abs(a["costs"] - b["costs"]) / np.maximum(1.0, np.abs(b["costs"]))
+    print(f"\ntcgen05 vs mma.sync costs: max rel {rel.max():.2e}, median {np.median(rel):.2e}")
+    assert rel.max() <= 1e-4
 
 
 def run_opts(m, p, precision, **kw):
@@ -86,7 +118,7 @@ def test_bf16_mlp_warp_pairs_block_sizes(m, bt, K, T):
     at every block size, with ragged K (samples beyond K computed and
     discarded) and horizons that end inside a ring half or on its edge."""
     p = as_f32_problem(W.bicycle_mlp(K=K, T=T, lam=100.0))
-    g = run_opts(m, p, m.MPPI_PREC_BF16_MLP, block_threads=bt)
+    g = run_opts(m, p, m.MPPI_PREC_BF16_MLP, block_threads=bt, rollout_variant=1)
     o = oracle.mppi_step(p, n_threads=n_threads(), want_eps=True)
     check_costs(p, g["costs"], o["S"], bf16=True)
     w_ref, st_ref, _ = oracle.weights(g["costs"], 100.0)
@@ -97,4 +129,8 @@ def test_bf16_mlp_warp_pairs_block_sizes(m, bt, K, T):
 def test_bf16_mlp_rejects_odd_warp_count(m):
     p = as_f32_problem(W.bicycle_mlp(K=256, T=8, lam=1.0))
     with pytest.raises(Exception):
-        m.MPPI.from_problem(p, precision=m.MPPI_PREC_BF16_MLP, block_threads=96)
+        m.MPPI.from_problem(p, precision=m.MPPI_PREC_BF16_MLP, block_threads=96,
+                            rollout_variant=1)
+    with pytest.raises(Exception):     # the tcgen05 kernel has one block shape
+        m.MPPI.from_problem(p, precision=m.MPPI_PREC_BF16_MLP, block_threads=128,
+                            rollout_variant=2)
