@@ -327,10 +327,14 @@ MPPI_API mppi_status mppi_sample_noise(uint64_t seed, uint64_t step, int K, int 
  * QUADROTOR + QUADRATIC or QUAD_OBSTACLES (at most 32 spheres) + RK4.
  * The device buffers named in the descriptors are fixed at creation (the
  * graph refers to them) and must outlive the batch.  mppi_batch_create picks
- * the block size by timing 64/128/256-thread candidates on the device unless
- * opt->block_threads gives one (the result is cached per workload in the
- * process); it synchronises the device.  opt->beta is not used (each
- * descriptor carries its own). */
+ * the block size (64/128/256 threads) and the tile order (longest tiles first,
+ * or instances by ascending cost so that cheap instances complete early) by
+ * timing the candidates on the device unless opt->block_threads gives the
+ * block size (then instances by ascending cost); the result is cached per
+ * workload in the process.  An instance whose non-zero weights are few is
+ * updated by the block that finishes its last rollout tile, so its latency
+ * (mppi_batch_latency) ends there; it synchronises the device.  opt->beta is
+ * not used (each descriptor carries its own). */
 typedef struct mppi_batch mppi_batch;
 
 typedef struct {

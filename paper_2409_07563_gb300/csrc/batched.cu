@@ -2,18 +2,24 @@
 // persistent launch pair, captured in a CUDA graph (step a7).
 //
 // Kernel A (rollout): a grid of one or a few blocks per SM pulls work items
-// (instance, tile of samples) from an atomic head over a list sorted by
-// estimated cost (longest first).  Cart-pole tiles run one sample per
+// (instance, tile of samples) from an atomic head over a list in one of two
+// orders (tiles longest first, or instances by ascending cost with each
+// instance's tiles together; the autotuner keeps the second unless it is
+// more than 2 % slower).  Cart-pole tiles run one sample per
 // thread; quadrotor tiles run one sample per thread on four warp roles per 32
 // samples (quad_pair.cuh) when the block has 128 or 256 threads, else four
 // lanes per sample (quad_group.cuh).  Each tile
 // leaves (rho_b, eta_b, eta2_b); the last tile of an instance to finish
 // (per-instance ticket, nobody waits) merges its instance's partials into
 // rho, eta, F, ESS (Eq. 17-18, Eq. 4), writes the weights and an
-// order-preserving list of the samples whose weight is not zero.
-// Kernel B (update): items (instance, Philox-block tile) regenerate the
-// noise of those samples only and write u_new (Algorithm 1 update); the last
-// item of an instance stamps its completion time and advances its counter.
+// order-preserving list of the samples whose weight is not zero; when that
+// list is short it also applies the instance's update (Algorithm 1) and
+// stamps the instance complete, so an instance's latency ends with its own
+// last tile.
+// Kernel B (update): items (instance, Philox-block tile) of the remaining
+// instances regenerate the noise of the listed samples only and write u_new;
+// the last item of an instance stamps its completion time and advances its
+// counter.
 // Block shape is chosen by timing candidates on the device (autotuner) and
 // cached per workload signature.  No kernel waits on another block.
 #include <cuda_runtime.h>
@@ -39,6 +45,9 @@ namespace {
 
 enum { kKindCartpole = 0, kKindQuad = 1 };
 constexpr int kBatchQb = 2;    // Philox blocks per update item
+// Up to this many Philox calls per thread, the block that finishes an
+// instance's last rollout tile applies its update itself.
+constexpr int kBatchInlineCalls = 8;
 constexpr int kBatchRed = 64;  // reduction scratch floats
 // shared memory of the quadrotor warp groups: spheres (kPairSpheres float4)
 // then kPairGroupFloats per group of four warps
@@ -57,7 +66,7 @@ struct DevInst {
     unsigned long long seed;
     const float *x0, *u_nom, *dyn, *cost;
     float *u_new, *stats;
-    float *S, *w, *part, *scal;  // scal: rho, eta, F, ess, valid, nnz
+    float *S, *w, *part, *scal;  // scal: rho, eta, F, ess, valid, nnz, updated inline
     int *nz;
     unsigned int *tick;          // [2]
     unsigned long long *counter, *done_ns;
@@ -126,8 +135,45 @@ __device__ void finish_instance(const DevInst &I, float *red) {
         }
     }
     __syncthreads();
+    // A short non-zero list: this block applies the instance's update itself
+    // (u_new = u_nom + sum_k w_k eps_k over the list, every Philox block of
+    // the instance) and completes the instance now, so its latency ends with
+    // its own last tile; otherwise the update kernel's items do it.
+    const int nnz = s_base;
+    const int QT = (I.T + 3) / 4, Q = I.nu * QT;
+    const bool inline_update = ok && nnz * ((Q + static_cast<int>(blockDim.x) - 1) /
+                                            static_cast<int>(blockDim.x)) <= kBatchInlineCalls;
+    if (inline_update) {
+        const NoiseKey nk = make_noise_key(I.seed, *I.counter);
+        for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+            const int j = q / QT, t0 = 4 * (q % QT);
+            const float sig = I.sigma[j];
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int idx = 0; idx < nnz; ++idx) {
+                const int k = I.nz[idx];
+                const float w = I.w[k];
+                float z[4];
+                box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(q)), z);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] += w * (sig * z[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (t0 + i < I.T) {
+                    const int o = (t0 + i) * I.nu + j;
+                    I.u_new[o] = I.u_nom[o] + acc[i];
+                }
+        }
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
         const float inf = __int_as_float(0x7f800000);
+        I.scal[6] = inline_update ? 1.f : 0.f;  // the update kernel skips the instance
+        if (inline_update) {
+            __threadfence();
+            *I.done_ns = global_ns();
+            *I.counter += 1ull;
+        }
         I.scal[0] = ok ? rho : inf;
         I.scal[1] = ok ? eta_v : 0.f;
         I.scal[2] = ok ? rho - I.lambda * logf(eta_v / static_cast<float>(I.K)) : inf;
@@ -263,6 +309,10 @@ __global__ void __launch_bounds__(256) batch_update_kernel(const DevInst *insts,
         if (it >= n_items) break;
         const Item item = items[it];
         const DevInst &I = insts[item.inst];
+        if (__ldcg(I.scal + 6) != 0.f) {  // the rollout kernel applied the update
+            __syncthreads();                // (s_item is rewritten next iteration)
+            continue;
+        }
         const int QT = (I.T + 3) / 4, Q = I.nu * QT, q0 = item.tile * kBatchQb;
         const int nnz = static_cast<int>(__ldcg(I.scal + 5));
         const NoiseKey nk = make_noise_key(I.seed, *I.counter);
@@ -337,6 +387,7 @@ struct mppi_batch {
     mppi::Item *items = nullptr;        // rollout items then update items
     int n_roll = 0, n_upd = 0;
     int threads = 128, grid_a = 0, grid_b = 0;
+    int order = 1;                      // rollout tile order (plan_items)
     int smem_u = 0, smem_cost = 0;
     size_t smem_bytes = 0;
     cudaStream_t cap = nullptr;
@@ -350,7 +401,7 @@ namespace mppi {
 namespace {
 
 std::mutex g_tune_mutex;
-std::map<std::string, int> g_tuned;  // workload signature -> block threads
+std::map<std::string, std::pair<int, int>> g_tuned;  // workload signature -> (threads, order)
 
 std::string signature(const mppi_batch &b) {
     std::string s;
@@ -360,13 +411,20 @@ std::string signature(const mppi_batch &b) {
     return s;
 }
 
-// Tile sizes and work lists for a block of `threads` threads.
-void plan_items(mppi_batch &b, int threads, std::vector<Item> &roll, std::vector<Item> &upd) {
+// Tile sizes and work lists for a block of `threads` threads.  Order 0:
+// tiles longest first (the classic makespan heuristic; every instance then
+// finishes near the end of the step).  Order 1: instances by ascending total
+// cost, each instance's tiles consecutive, so cheap instances complete early
+// (their update follows their last tile) and the step's end holds only the
+// last, largest instances' small tiles.
+void plan_items(mppi_batch &b, int threads, int order, std::vector<Item> &roll,
+                std::vector<Item> &upd) {
     struct Est {
         double cost;
         Item it;
     };
     std::vector<Est> est;
+    std::vector<std::pair<double, int>> inst_cost;
     roll.clear();
     upd.clear();
     for (int i = 0; i < b.n; ++i) {
@@ -377,17 +435,26 @@ void plan_items(mppi_batch &b, int threads, std::vector<Item> &roll, std::vector
         // relative cost of one tile: time steps x per-step weight of the model
         const double w = h.kind == kKindCartpole ? 1.0 : 3.0;
         for (int t = 0; t < d.n_tiles; ++t) est.push_back({w * h.T, Item{i, t}});
+        inst_cost.push_back({w * h.T * d.n_tiles, i});
         const int Q = h.nu * ((h.T + 3) / 4);
         d.q_tiles = (Q + kBatchQb - 1) / kBatchQb;
         for (int t = 0; t < d.q_tiles; ++t) upd.push_back(Item{i, t});
     }
-    std::stable_sort(est.begin(), est.end(), [](const Est &a, const Est &c) { return a.cost > c.cost; });
-    for (const Est &e : est) roll.push_back(e.it);
+    if (order == 0) {
+        std::stable_sort(est.begin(), est.end(),
+                         [](const Est &a, const Est &c) { return a.cost > c.cost; });
+        for (const Est &e : est) roll.push_back(e.it);
+    } else {
+        std::stable_sort(inst_cost.begin(), inst_cost.end());
+        for (const auto &ic : inst_cost)
+            for (int t = 0; t < b.dev_h[ic.second].n_tiles; ++t) roll.push_back(Item{ic.second, t});
+    }
 }
 
-cudaError_t upload_plan(mppi_batch &b, int threads) {
+cudaError_t upload_plan(mppi_batch &b, int threads, int order) {
     std::vector<Item> roll, upd;
-    plan_items(b, threads, roll, upd);
+    plan_items(b, threads, order, roll, upd);
+    b.order = order;
     b.n_roll = static_cast<int>(roll.size());
     b.n_upd = static_cast<int>(upd.size());
     roll.insert(roll.end(), upd.begin(), upd.end());
@@ -442,30 +509,34 @@ cudaError_t batch_tune(mppi_batch &b) {
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tuned.find(sig);
-        if (it != g_tuned.end()) return upload_plan(b, it->second);
+        if (it != g_tuned.end()) return upload_plan(b, it->second.first, it->second.second);
     }
+    // block shape x tile order, by timing three steps of each on the device;
+    // the instance-ordered plan (low per-instance latency) is kept unless it
+    // is more than 2 % slower than the best longest-tile-first plan
     const int cand[] = {64, 128, 256};
-    float best = 1e30f;
-    int best_t = 128;
+    float best[2] = {1e30f, 1e30f};
+    int best_t[2] = {128, 128};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaError_t e = cudaSuccess;
-    for (int t : cand) {
-        if ((e = upload_plan(b, t)) != cudaSuccess) break;
-        if ((e = batch_enqueue(b, b.cap)) != cudaSuccess) break;  // warm-up
-        cudaEventRecord(e0, b.cap);
-        for (int r = 0; r < 3; ++r)
-            if ((e = batch_enqueue(b, b.cap)) != cudaSuccess) break;
-        cudaEventRecord(e1, b.cap);
-        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            best_t = t;
+    for (int order = 0; order < 2 && e == cudaSuccess; ++order)
+        for (int t : cand) {
+            if ((e = upload_plan(b, t, order)) != cudaSuccess) break;
+            if ((e = batch_enqueue(b, b.cap)) != cudaSuccess) break;  // warm-up
+            cudaEventRecord(e0, b.cap);
+            for (int r = 0; r < 3; ++r)
+                if ((e = batch_enqueue(b, b.cap)) != cudaSuccess) break;
+            cudaEventRecord(e1, b.cap);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best[order]) {
+                best[order] = ms;
+                best_t[order] = t;
+            }
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return e;
@@ -473,11 +544,12 @@ cudaError_t batch_tune(mppi_batch &b) {
     if ((e = cudaMemsetAsync(b.u64, 0, b.n * sizeof(unsigned long long), b.cap)) != cudaSuccess)
         return e;
     if ((e = cudaStreamSynchronize(b.cap)) != cudaSuccess) return e;
+    const int order = best[1] <= 1.02f * best[0] ? 1 : 0;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tuned[sig] = best_t;
+        g_tuned[sig] = {best_t[order], order};
     }
-    return upload_plan(b, best_t);
+    return upload_plan(b, best_t[order], order);
 }
 
 }  // namespace mppi
@@ -656,7 +728,7 @@ mppi_status mppi_batch_create(int n, const mppi_instance_desc *desc, const mppi_
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     }
     if (e == cudaSuccess)
-        e = o.block_threads ? mppi::upload_plan(*b, o.block_threads) : mppi::batch_tune(*b);
+        e = o.block_threads ? mppi::upload_plan(*b, o.block_threads, 1) : mppi::batch_tune(*b);
     if (e == cudaSuccess) e = mppi::batch_capture(*b);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
