@@ -20,6 +20,7 @@ constexpr int kMaxK = 1 << 24;
 constexpr int kUpdateThreads = 256;
 constexpr int kUpdateQb = 2;          // Philox blocks (4 elements each) per update block
 constexpr int kMaxUpdateChunks = 64;  // split-K factor cap of the update
+constexpr int kUpdateCallsPerThread = 8;  // Philox calls per update thread before another chunk
 
 // Device scratch owned by a context.
 struct Scratch {

@@ -8,9 +8,12 @@
 // contributes exactly zero).  eps is regenerated from the same Philox counter
 // the rollout used (bit-identical FP32 product sigma_j * z), never read from
 // memory: Philox block q holds channel j = q / QT at steps 4 (q % QT) .. + 3.
-// Grid: (Philox-block tiles) x (chunks of the non-zero list); each block
-// reduces its partial sums and the last block to finish (atomic ticket) adds
-// the chunks in a fixed order, so the result is deterministic.  When the
+// Grid: (Philox-block tiles) x (chunks of the non-zero list); only as many
+// chunks work as the list needs (at most kUpdateCallsPerThread Philox calls
+// per thread).  With one chunk each block writes its tiles of u_new itself;
+// otherwise each block reduces its partial sums and the last block to finish
+// (atomic ticket) adds the chunks in a fixed order, so the result is
+// deterministic.  When the
 // list was short the rollout already applied the update and every block
 // returns at once.
 #include "device_common.cuh"
@@ -45,7 +48,14 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
     const int nnz = static_cast<int>(p.scalars[5]);
     const bool list = nnz >= 0;
     const int n = list ? nnz : p.K;
-    const int len = (n + gridDim.y - 1) / gridDim.y;
+    // chunks in use: a listed update needs only enough of them that a thread
+    // makes at most kUpdateCallsPerThread Philox calls; the others return
+    const int ny = list ? max(1, min(static_cast<int>(gridDim.y),
+                                     (nnz * QB + kUpdateThreads * kUpdateCallsPerThread - 1) /
+                                         (kUpdateThreads * kUpdateCallsPerThread)))
+                        : static_cast<int>(gridDim.y);
+    if (static_cast<int>(blockIdx.y) >= ny) return;
+    const int len = (n + ny - 1) / ny;
     const int i_begin = blockIdx.y * len, i_end = min(n, i_begin + len);
     const NoiseKey nk = make_noise_key(p.seed, *p.counter);
 
@@ -110,28 +120,37 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
         float v = 0.f;
         for (int w = 0; w < kUpdateThreads / kWarp; ++w) v += s_red[w][threadIdx.x];
         const int q = q0 + threadIdx.x / 4;
-        if (q < Q)
-            p.upartials[(static_cast<size_t>(blockIdx.y) * Q + q) * 4 + threadIdx.x % 4] = v;
+        if (q < Q) {
+            if (ny == 1) {  // one chunk: this block's sums are the update
+                const int j = q / QT, t = 4 * (q % QT) + threadIdx.x % 4;
+                if (t < p.T) {
+                    const int o = t * NU + j;
+                    p.u_new[o] = p.u_nom[o] + p.gamma * v;
+                }
+            } else {
+                p.upartials[(static_cast<size_t>(blockIdx.y) * Q + q) * 4 + threadIdx.x % 4] = v;
+            }
+        }
     }
     // the barrier orders every writer's partial before thread 0's device-scope
-    // fence (cumulative), and so before the ticket
+    // fence (cumulative), and so before the ticket; the last block (which
+    // also knows that every block has read the step counter) advances it
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned int ticket = atomicAdd(p.tickets + 1, 1u);
-        s_last = (ticket == gridDim.x * gridDim.y - 1);
+        s_last = (ticket == gridDim.x * static_cast<unsigned int>(ny) - 1);
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
 
     // last block: combine chunks in order and write u_new
-    for (int el = threadIdx.x; el < 4 * Q; el += blockDim.x) {
+    for (int el = threadIdx.x; ny > 1 && el < 4 * Q; el += blockDim.x) {
         const int q = el / 4, j = q / QT, t = 4 * (q % QT) + el % 4;
         if (t >= p.T) continue;
         // chunk partials added in chunk order; the loads of eight chunks are
         // issued together so their latencies overlap
-        const int ny = static_cast<int>(gridDim.y);
         float sum = 0.f;
         int c = 0;
         for (; c + 8 <= ny; c += 8) {
