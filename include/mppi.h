@@ -65,7 +65,11 @@ typedef enum {
     MPPI_ERR_OOM = 3,           /* device allocation failed */
     MPPI_ERR_UNSUPPORTED = 4,   /* valid request this build does not implement */
     MPPI_ERR_NUMERIC = 5,       /* every sample cost was non-finite */
-    MPPI_ERR_TIMEOUT = 6        /* a bounded device wait gave up */
+    MPPI_ERR_TIMEOUT = 6,       /* a bounded device wait gave up (the tcgen05 MLP
+                                   kernel's mbarrier waits, 0.2 s each); no other
+                                   kernel waits on anything */
+    MPPI_ERR_CHECK = 7          /* checked mode: a device-side index fell outside
+                                   its array; the access was skipped */
 } mppi_status;
 
 /* Dynamics (state / control layouts and parameter arrays):
@@ -178,7 +182,14 @@ typedef struct {
                                  dynamics warp, a noise warp and a cost warp per 32
                                  samples (block_threads 96 or 192, else one sample
                                  per thread), 1 one sample per thread */
-    int reserved[6];
+    int checked;              /* 1: every kernel that indexes memory from computed data
+                                 (costmap cells, candidate slots, the non-zero weight
+                                 list) checks the index first and, when it is out of
+                                 range, skips the access and sets MPPI_ERR_CHECK in
+                                 the status word (mppi_poll_status); 0 (default):
+                                 the indices are correct by construction and are not
+                                 checked */
+    int reserved[5];
 } mppi_options;
 
 /* Fills *opt with the defaults (beta 1, FP32, seed 0, automatic launch). */
@@ -225,6 +236,16 @@ MPPI_API mppi_status mppi_step_host(mppi_ctx *ctx, const float *x0_h, const floa
  * create; NULL keeps the current one).  Synchronises the stream, then copies;
  * later steps use the new values. */
 MPPI_API mppi_status mppi_set_params(mppi_ctx *ctx, const float *dyn_params, const float *cost_params);
+
+/* Replaces the parameter arrays from DEVICE memory (same lengths as at
+ * create; NULL keeps the current one) with an asynchronous device-to-device
+ * copy on the context's stream: no host synchronisation, later steps on that
+ * stream use the new values.  The values are not validated and the context's
+ * host copy is not updated (mppi_set_params overwrites both).  Cost arrays of
+ * QUADROTOR contexts give MPPI_ERR_UNSUPPORTED (their kernels take the cost
+ * constants from the host copy). */
+MPPI_API mppi_status mppi_set_params_device(mppi_ctx *ctx, const float *dyn_params_d,
+                                            const float *cost_params_d);
 
 /* Gradient of L = sum_{t,j} grad_u_new[t,j] u_new[t,j] of the most recent
  * mppi_step with respect to theta = (Q[0..3], R, l, m_cart) at fixed noise

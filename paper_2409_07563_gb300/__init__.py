@@ -61,7 +61,7 @@ class MPPI:
 
     def __init__(self, *, dyn_kind, integrator, nx, nu, dyn_params, cost_kind, cost_params,
                  K, T, dt, lam, sigma, beta=1, seed=0, cost_map=None,
-                 precision=MPPI_PREC_FP32, block_threads=0, rollout_variant=0):
+                 precision=MPPI_PREC_FP32, block_threads=0, rollout_variant=0, checked=0):
         L = load()
         self._dyn_params = _f32(dyn_params)
         self._cost_params = _f32(cost_params)
@@ -82,6 +82,7 @@ class MPPI:
         opt.precision = int(precision)
         opt.block_threads = int(block_threads)
         opt.rollout_variant = int(rollout_variant)
+        opt.checked = int(checked)
         h = ctypes.c_void_p()
         st = L.mppi_create(ctypes.byref(dyn), ctypes.byref(cost), int(K), int(T), float(dt),
                            float(lam), _fptr(self._sigma), ctypes.byref(opt), ctypes.byref(h))
@@ -189,6 +190,16 @@ class MPPI:
         c = None if cost_params is None else _f32(cost_params)
         check(L.mppi_set_params(self._h, None if d is None else _fptr(d),
                                 None if c is None else _fptr(c)), "mppi_set_params", self._h)
+
+    def set_params_device(self, dyn_params=None, cost_params=None, stream=None):
+        """``mppi_set_params_device``: new parameter arrays from CUDA float32
+        tensors, copied device to device on the stream (no host sync)."""
+        L = load()
+        _check_tensor(dyn_params, len(self._dyn_params), "dyn_params")
+        _check_tensor(cost_params, len(self._cost_params), "cost_params")
+        self._use_stream(L, stream)
+        check(L.mppi_set_params_device(self._h, _dptr(dyn_params), _dptr(cost_params)),
+              "mppi_set_params_device", self._h)
 
     def backward(self, grad_u_new, stream=None):
         """``mppi_step_backward``: gradient of sum(grad_u_new * u_new) of the last
@@ -349,10 +360,14 @@ def _make_step_function():
         @staticmethod
         def forward(ctx, theta, x0, u_nom, ctl):
             th = theta.detach().to(torch.float32).contiguous()
-            base = (torch.tensor(ctl._dyn_params, device=th.device),
-                    torch.tensor(ctl._cost_params, device=th.device))
+            base = getattr(ctl, "_theta_base", None)
+            if base is None or base[0].device != th.device:
+                base = (torch.tensor(ctl._dyn_params, device=th.device),
+                        torch.tensor(ctl._cost_params, device=th.device))
+                ctl._theta_base = base
             dyn, cost = _theta_params(base, th)
-            ctl.set_params(dyn.cpu().numpy(), cost.cpu().numpy())
+            # device-to-device on the stream: theta never goes through the host
+            ctl.set_params_device(dyn, cost)
             out = ctl.step(x0, u_nom)
             ctx.ctl = ctl
             ctx.counter = ctl.counter

@@ -45,7 +45,7 @@ class CostDesc(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_int), ("precision", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("block_threads", ctypes.c_int), ("rollout_variant", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("checked", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class InstanceDesc(ctypes.Structure):
@@ -79,6 +79,7 @@ def load() -> ctypes.CDLL:
     L.mppi_step.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.mppi_step_host.argtypes = [vp, c_float_p, c_float_p, c_float_p, c_float_p]
     L.mppi_set_params.argtypes = [vp, c_float_p, c_float_p]
+    L.mppi_set_params_device.argtypes = [vp, vp, vp]
     L.mppi_step_backward.argtypes = [vp, vp, vp]
     L.mppi_get_counter.argtypes = [vp, ctypes.POINTER(u64)]
     L.mppi_set_counter.argtypes = [vp, u64]
@@ -93,7 +94,8 @@ def load() -> ctypes.CDLL:
     L.mppi_shift.argtypes = [vp, vp, i, vp]
     L.mppi_set_cem.argtypes = [vp, ctypes.c_float]
     for name in ("mppi_create", "mppi_set_stream", "mppi_step", "mppi_step_host",
-                 "mppi_set_params", "mppi_step_backward", "mppi_get_counter",
+                 "mppi_set_params", "mppi_set_params_device", "mppi_step_backward",
+                 "mppi_get_counter",
                  "mppi_set_counter", "mppi_poll_status", "mppi_sample_noise", "mppi_profile",
                  "mppi_profile_read", "mppi_set_iterations", "mppi_nominal_trajectory",
                  "mppi_shift", "mppi_set_cem"):

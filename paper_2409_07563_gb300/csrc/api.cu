@@ -226,6 +226,7 @@ StepParams make_params(const mppi_ctx &c) {
     p.counter = c.scr.counter;
     p.last_step = c.scr.last_step;
     p.saved_in = c.differentiable ? c.scr.saved_in : nullptr;
+    p.checked = c.checked;
     return p;
 }
 
@@ -317,6 +318,7 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     for (int j = 0; j < nu; ++j)
         if (!std::isfinite(sigma[j]) || sigma[j] < 0.f) return MPPI_ERR_INVALID_ARG;
     if (o.beta != 0 && o.beta != 1) return MPPI_ERR_INVALID_ARG;
+    if (o.checked != 0 && o.checked != 1) return MPPI_ERR_INVALID_ARG;
     if (o.block_threads < 0 || o.block_threads % 32 != 0 ||
         o.block_threads > (o.rollout_variant == 3 ? 512 : 256))
         return MPPI_ERR_INVALID_ARG;
@@ -358,6 +360,7 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     c->precision = o.precision;
     c->block_threads = o.block_threads;
     c->variant_opt = o.rollout_variant;
+    c->checked = o.checked;
     c->dt = dt;
     c->lambda = lambda;
     c->seed = o.seed;
@@ -553,6 +556,23 @@ mppi_status mppi_step_host(mppi_ctx *ctx, const float *x0_h, const float *u_nom_
     return MPPI_OK;
 }
 
+mppi_status mppi_set_params_device(mppi_ctx *ctx, const float *dyn_params_d,
+                                   const float *cost_params_d) {
+    if (!ctx) return MPPI_ERR_INVALID_ARG;
+    if (cost_params_d && ctx->dyn_kind == MPPI_DYN_QUADROTOR)
+        return fail(ctx, MPPI_ERR_UNSUPPORTED,
+                    "quadrotor cost constants are staged from the host copy: use mppi_set_params");
+    cudaError_t e = cudaSuccess;
+    if (dyn_params_d)
+        e = cudaMemcpyAsync(ctx->d_dyn, dyn_params_d, ctx->dyn_params_h.size() * sizeof(float),
+                            cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess && cost_params_d)
+        e = cudaMemcpyAsync(ctx->d_cost, cost_params_d, ctx->cost_params_h.size() * sizeof(float),
+                            cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "parameter copy");
+    return MPPI_OK;
+}
+
 mppi_status mppi_set_params(mppi_ctx *ctx, const float *dyn_params, const float *cost_params) {
     if (!ctx) return MPPI_ERR_INVALID_ARG;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -689,8 +709,10 @@ mppi_status mppi_poll_status(mppi_ctx *ctx) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");
     for (int code = 1; code < 32; ++code)
         if (word & (1u << code)) {
-            ctx->err = code == MPPI_ERR_NUMERIC ? "every sample cost was non-finite"
-                                                : "device-side error";
+            ctx->err = code == MPPI_ERR_NUMERIC   ? "every sample cost was non-finite"
+                       : code == MPPI_ERR_TIMEOUT ? "a bounded device wait gave up"
+                       : code == MPPI_ERR_CHECK   ? "checked mode: a device index was out of range"
+                                                  : "device-side error";
             return static_cast<mppi_status>(code);
         }
     return MPPI_OK;

@@ -39,7 +39,7 @@ __device__ __forceinline__ float bicycle_cost_warp(const StepParams &p, const fl
     const int T = p.T;
     const int nh = (T + kMlpH - 1) / kMlpH;
     const NoiseKey nk = make_noise_key(p.seed, *p.counter);
-    const CostCtx cc{p.map, p.map_h, p.map_w};
+    const CostCtx cc{p.map, p.map_h, p.map_w, p.checked ? p.status : nullptr};
     const float sig0 = p.sigma[0], sig1 = p.sigma[1], iv0 = p.ivar[0], iv1 = p.ivar[1];
     const int QT = (T + 3) / 4;
     CompSum J;

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
+#include "mppi.h"
 
 namespace mppi {
 
@@ -250,7 +251,13 @@ struct LinearDyn {
 struct CostCtx {
     const float *map;
     int map_h, map_w;
+    unsigned int *check = nullptr;  // checked mode: the status word, else null
 };
+
+// Checked mode: record an out-of-range index in the status word.
+__device__ __forceinline__ void flag_check(unsigned int *status) {
+    atomicOr(status, 1u << MPPI_ERR_CHECK);
+}
 
 // params [Q(NX), R(NU), goal(NX), s]
 template <int NX, int NU>
@@ -342,8 +349,13 @@ __device__ __forceinline__ float costmap_bilinear(float x, float y, float x_min,
     float gy = (y - y_min) * inv_cell - 0.5f;
     gx = fminf(fmaxf(gx, 0.0f), static_cast<float>(W - 1));
     gy = fminf(fmaxf(gy, 0.0f), static_cast<float>(H - 1));
-    const int j0 = min(static_cast<int>(floorf(gx)), W - 2);
-    const int i0 = min(static_cast<int>(floorf(gy)), H - 2);
+    int j0 = min(static_cast<int>(floorf(gx)), W - 2);
+    int i0 = min(static_cast<int>(floorf(gy)), H - 2);
+    if (cc.check && !(j0 >= 0 && j0 <= W - 2 && i0 >= 0 && i0 <= H - 2)) {
+        flag_check(cc.check);
+        j0 = 0;
+        i0 = 0;
+    }
     const float fx = gx - static_cast<float>(j0), fy = gy - static_cast<float>(i0);
     const float *m = cc.map + static_cast<size_t>(i0) * W + j0;
     const float a = __ldg(m), b = __ldg(m + 1), c = __ldg(m + W), d = __ldg(m + W + 1);

@@ -64,6 +64,7 @@ struct StepParams {
     float *saved_in;                    // non-null: block 0 of the rollout copies x0, u_nom here
     unsigned int *tickets, *status;
     unsigned long long *counter, *last_step;
+    int checked;                        // check computed indices (mppi_options.checked)
 };
 
 enum RolloutVariant {
@@ -99,7 +100,7 @@ struct ProfileRecord {
 
 struct mppi_ctx {
     int dyn_kind = 0, integrator = 0, nx = 0, nu = 0, cost_kind = 0;
-    int K = 0, T = 0, beta = 1, precision = 0, block_threads = 0, variant_opt = 0;
+    int K = 0, T = 0, beta = 1, precision = 0, block_threads = 0, variant_opt = 0, checked = 0;
     float dt = 0.f, lambda = 1.f;
     uint64_t seed = 0;
     std::vector<float> sigma, dyn_params_h, cost_params_h;

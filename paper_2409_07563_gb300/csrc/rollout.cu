@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256) rollout_kernel(const StepParams p) {
         for (int i = tid; i < p.T * NU; i += nt) p.saved_in[NX + i] = s_u[i];
     }
     const SampleArgs args{p.T, p.dt, p.lam_beta, p.sigma, p.ivar, p.x0, s_u, s_dyn, s_cost,
-                          CostCtx{p.map, p.map_h, p.map_w}, make_noise_key(p.seed, *p.counter)};
+                          CostCtx{p.map, p.map_h, p.map_w, p.checked ? p.status : nullptr}, make_noise_key(p.seed, *p.counter)};
     const int k = blockIdx.x * nt + tid;
     float S = __int_as_float(0x7f800000);  // inactive lanes take no part
     if (k < p.K) {
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) pair_rollout_kernel(const StepParams p) {
             pair_sync(bar_id);
         }
     } else {
-        const CostCtx cc{p.map, p.map_h, p.map_w};
+        const CostCtx cc{p.map, p.map_h, p.map_w, p.checked ? p.status : nullptr};
         float ivar[NU];
 #pragma unroll
         for (int j = 0; j < NU; ++j) ivar[j] = p.ivar[j];

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) bicycle_mlp_f32_kernel(const StepParams p
 
     const int k0 = (blockIdx.x * (nt / kWarp) + warp) * (kSamplesPerWarp * kSt) + q;
     const NoiseKey nk = make_noise_key(p.seed, *p.counter);
-    const CostCtx cc{p.map, p.map_h, p.map_w};
+    const CostCtx cc{p.map, p.map_h, p.map_w, p.checked ? p.status : nullptr};
     const float sig0 = p.sigma[0], sig1 = p.sigma[1], iv0 = p.ivar[0], iv1 = p.ivar[1];
     const int QT = (T + 3) / 4;
     // activations of slot j: ex + j * 8 * 68

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "device_common.cuh"
+#include "models.cuh"
 #include "mppi_internal.h"
 
 namespace mppi {
@@ -147,6 +148,10 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, int ca
 #pragma unroll
         for (int j = 0; j < kListPerThread; ++j) {
             if (i0 + j < i1 && w[j] != 0.f) {
+                if (p.checked && !(at < p.K && e[j].x >= 0 && e[j].x < p.K)) {
+                    flag_check(p.status);
+                    continue;
+                }
                 p.nz[at] = e[j].x;
                 p.w[at] = w[j];
                 if (at < kInlineUpdateCalls) {
@@ -164,6 +169,10 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, int ca
             const int c = static_cast<int>(__ldcg(p.partials + 4 * b + 3));
             for (int j = 0; j < c; ++j) {
                 const int2 ent = __ldcg(cand2 + off + j);
+                if (p.checked && !(pos < p.K)) {
+                    flag_check(p.status);
+                    break;
+                }
                 p.nz[pos] = ent.x;
                 p.w[pos] = expf(-(__int_as_float(ent.y) - rho) / p.lambda) / eta_v;
                 ++pos;
@@ -190,6 +199,10 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, int ca
 #pragma unroll
         for (int i = 0; i < kListPerThread; ++i) {
             if (c_begin + i < c_end && ww[i] != 0.f) {
+                if (p.checked && !(at < p.K && kk[i] >= 0 && kk[i] < p.K)) {
+                    flag_check(p.status);
+                    continue;
+                }
                 p.nz[at] = kk[i];
                 p.w[at] = ww[i];
                 if (at < kInlineUpdateCalls) {
@@ -291,9 +304,14 @@ __device__ inline void block_weight_tail(const StepParams &p, float S, int k, fl
     const bool cand = k >= 0 && is_finite(Sf) && (Sf - gmin) < kCandidateSpan * p.lambda;
     int n_cand;
     const int slot = block_exclusive_scan(cand ? 1 : 0, reinterpret_cast<int *>(s_red), n_cand);
-    if (cand)
-        reinterpret_cast<int2 *>(p.cand)[static_cast<size_t>(blockIdx.x) * cand_stride + slot] =
-            make_int2(k, __float_as_int(Sf));
+    if (cand) {
+        if (p.checked && slot >= cand_stride) {
+            flag_check(p.status);  // (a block never holds more than cand_stride samples)
+        } else {
+            reinterpret_cast<int2 *>(p.cand)[static_cast<size_t>(blockIdx.x) * cand_stride + slot] =
+                make_int2(k, __float_as_int(Sf));
+        }
+    }
     __shared__ bool s_last;
     // the barrier orders every thread's candidate write before thread 0's
     // device-scope fence (cumulative), and so before the ticket

@@ -17,6 +17,7 @@
 // list was short the rollout already applied the update and every block
 // returns at once.
 #include "device_common.cuh"
+#include "models.cuh"
 #include "mppi_internal.h"
 #include "rollout_tail.cuh"
 
@@ -80,8 +81,14 @@ __global__ void __launch_bounds__(kUpdateThreads) update_kernel(const StepParams
         }
     };
     if (list) {
-        for (int idx = i_begin + threadIdx.x; idx < i_end; idx += blockDim.x)
-            accumulate(__ldcg(p.nz + idx), __ldcg(p.w + idx));
+        for (int idx = i_begin + threadIdx.x; idx < i_end; idx += blockDim.x) {
+            const int k = __ldcg(p.nz + idx);
+            if (p.checked && !(k >= 0 && k < p.K)) {
+                flag_check(p.status);
+                continue;
+            }
+            accumulate(k, __ldcg(p.w + idx));
+        }
     } else {
         // every sample of the chunk: the weights of eight samples per thread
         // at a time (their cost loads in flight together), then the noise of

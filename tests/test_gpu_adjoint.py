@@ -117,3 +117,32 @@ def test_backward_unsupported_models_raise(m):
     ctl.step(x0, u)
     with pytest.raises(m.MPPIError):
         ctl.backward(torch.zeros(40, device="cuda"))
+
+
+def test_device_parameter_copy_equals_host_copy(m):
+    """mppi_set_params_device (used by MPPIStep.forward) gives the step the
+    same parameters as mppi_set_params, without a host round trip; quadrotor
+    cost arrays are refused (their constants are staged from the host copy)."""
+    p = as_f32_problem(W.differentiable(K=1024, T=50))
+    dyn = p["dyn_params"].copy()
+    cost = p["cost_params"].copy()
+    dyn[2] *= 1.3      # pole length
+    cost[0] *= 2.0     # Q_x
+    x0 = torch.tensor(p["x0"], dtype=torch.float32, device="cuda")
+    u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device="cuda")
+    a = m.MPPI.from_problem(p)
+    b = m.MPPI.from_problem(p)
+    a.set_params(dyn, cost)
+    b.set_params_device(torch.tensor(dyn, dtype=torch.float32, device="cuda"),
+                        torch.tensor(cost, dtype=torch.float32, device="cuda"))
+    ra = a.step(x0, u, want_costs=True)
+    rb = b.step(x0, u, want_costs=True)
+    torch.cuda.synchronize()
+    assert torch.equal(ra["u_new"], rb["u_new"]) and torch.equal(ra["costs"], rb["costs"])
+    q = W.quadrotor(K=64, T=10)
+    c = m.MPPI.from_problem(q)
+    with pytest.raises(m.MPPIError):
+        c.set_params_device(cost_params=torch.tensor(q["cost_params"], dtype=torch.float32,
+                                                     device="cuda"))
+    c.set_params_device(dyn_params=torch.tensor(q["dyn_params"], dtype=torch.float32,
+                                                device="cuda"))
