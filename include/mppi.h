@@ -161,27 +161,25 @@ typedef struct {
     int beta;                 /* importance-sampling term: 1 (default) or 0 */
     int precision;            /* mppi_precision (default FP32) */
     uint64_t seed;            /* Philox key (default 0) */
-    int block_threads;        /* rollout block size (multiple of 32, <= 256; variant 3:
-                                 multiple of 64, <= 512; variant 4: 128 or 256;
-                                 BF16_MLP: 64, 128, 192 or 256, a dynamics warp
-                                 and a noise-and-cost warp per 32 samples);
-                                 0 = automatic */
+    int block_threads;        /* rollout block size (multiple of 32, <= 256; variant 4:
+                                 128 or 256; BF16_MLP with variant 0 or 1: 64, 128,
+                                 192 or 256, a dynamics warp and a noise-and-cost
+                                 warp per 32 samples); 0 = automatic */
     int rollout_variant;      /* 0 automatic, 1 one sample per thread, 2 four lanes per
-                                 sample, 3 four lanes per sample with a dynamics warp
-                                 and a cost warp per eight samples, 4 one sample per
-                                 thread with a dynamics warp, two noise warps and a
-                                 cost warp per 32 samples (2-4: QUADROTOR with at most
-                                 32 obstacles).  BICYCLE_MLP with COSTMAP_SPEED at
-                                 FP32: 0 takes four lanes per two samples (the
-                                 MLP's hidden units split over the lanes), 1 one
-                                 sample per thread.  BICYCLE_MLP at BF16_MLP: 0 (or
-                                 1) the warp-level mma.sync kernel, 2 the tcgen05
-                                 kernel (two 64-sample tiles per CTA, accumulators
-                                 in tensor memory, block_threads 0).  The other
-                                 models: 0 takes a
-                                 dynamics warp, a noise warp and a cost warp per 32
-                                 samples (block_threads 96 or 192, else one sample
-                                 per thread), 1 one sample per thread */
+                                 sample, 4 one sample per thread with a dynamics warp,
+                                 two noise warps and a cost warp per 32 samples (2, 4:
+                                 QUADROTOR with at most 32 obstacles; 3 is retired and
+                                 gives MPPI_ERR_UNSUPPORTED).  BICYCLE_MLP with
+                                 COSTMAP_SPEED at FP32: 0 takes four lanes per two
+                                 samples (the MLP's hidden units split over the
+                                 lanes), 1 one sample per thread.  BICYCLE_MLP at
+                                 BF16_MLP: 0 (or 1) the warp-level mma.sync kernel, 2
+                                 the tcgen05 kernel (two 64-sample tiles per CTA,
+                                 accumulators in tensor memory, block_threads 0).  The
+                                 other models: 0 takes a dynamics warp, a noise warp
+                                 and a cost warp per 32 samples (block_threads 96 or
+                                 192, else one sample per thread), 1 one sample per
+                                 thread */
     int checked;              /* 1: every kernel that indexes memory from computed data
                                  (costmap cells, candidate slots, the non-zero weight
                                  list) checks the index first and, when it is out of

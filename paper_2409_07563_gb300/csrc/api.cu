@@ -110,9 +110,7 @@ void plan_launch(mppi_ctx &c) {
     const int roles = mppi::quad_pair_roles(c);  // warps per 32 samples
     const bool pair1 = quad && asked == mppi::kVariantQuadPair &&
                        c.block_threads % (32 * roles) == 0 && mppi::quad_pair_applicable(c);
-    const bool split = quad && !pair1 && asked != mppi::kVariantQuadGroup &&
-                       c.block_threads % 64 == 0;
-    const bool group = quad && !pair1 && !split;
+    const bool group = quad && !pair1;
     const bool bf16 = c.precision == MPPI_PREC_BF16_MLP;
     // BF16 MLP: the warp-level mma.sync kernel by default (measured on GB300
     // at K = 16384, T = 100: 116 us against 198 for the tcgen05 kernel, whose
@@ -128,12 +126,10 @@ void plan_launch(mppi_ctx &c) {
                  : mlp32 ? mppi::kVariantMlpF32
                  : gpair ? mppi::kVariantGenericPair
                  : pair1 ? mppi::kVariantQuadPair
-                 : split ? mppi::kVariantQuadSplit
                  : group ? mppi::kVariantQuadGroup
                          : mppi::kVariantGeneric;
     // threads per sample (the FP32 MLP: four lanes per two samples)
-    const int lanes = mlp_tc ? 3 : mlp_sync || mlp32 ? 2 : gpair ? 3 : split ? 8 : pair1 ? roles
-                      : group ? 4 : 1;
+    const int lanes = mlp_tc ? 3 : mlp_sync || mlp32 ? 2 : gpair ? 3 : pair1 ? roles : group ? 4 : 1;
     const long threads_needed = static_cast<long>(c.K) * lanes;
     if (mlp_tc) {
         pl.rollout_threads = 384;  // two 64-sample tiles: 2 x 4 tile warps, four cost warps
@@ -166,12 +162,6 @@ void plan_launch(mppi_ctx &c) {
         const long groups = (static_cast<long>(c.K) + 31) / 32;
         const long per_sm = (groups + c.num_sms - 1) / c.num_sms;
         pl.rollout_threads = 32 * roles * static_cast<int>(std::min(2L, std::max(1L, per_sm)));
-    } else if (split) {
-        // one block per SM while the pairs fit eight to an SM, spread evenly
-        // (K = 8192: 1024 pairs, seven per block on 147 SMs); else four pairs
-        const long pairs = (static_cast<long>(c.K) + 7) / 8;
-        const long per_sm = (pairs + c.num_sms - 1) / c.num_sms;
-        pl.rollout_threads = per_sm <= 8 ? static_cast<int>(64 * per_sm) : 256;
     } else if (group) {
         pl.rollout_threads = 64;
     } else {
@@ -320,10 +310,12 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     if (o.beta != 0 && o.beta != 1) return MPPI_ERR_INVALID_ARG;
     if (o.checked != 0 && o.checked != 1) return MPPI_ERR_INVALID_ARG;
     if (o.block_threads < 0 || o.block_threads % 32 != 0 ||
-        o.block_threads > (o.rollout_variant == 3 ? 512 : 256))
+        o.block_threads > 256)
         return MPPI_ERR_INVALID_ARG;
     if (o.rollout_variant < 0 || o.rollout_variant > 4) return MPPI_ERR_INVALID_ARG;
-    if (o.rollout_variant == 3 && o.block_threads % 64 != 0) return MPPI_ERR_INVALID_ARG;
+    // rollout_variant 3 (four lanes per sample with a dynamics and a cost warp
+    // per eight samples) was retired: slower than the warp-role kernel
+    if (o.rollout_variant == 3) return MPPI_ERR_UNSUPPORTED;
     if (o.rollout_variant == 4 && o.block_threads % 128 != 0) return MPPI_ERR_INVALID_ARG;
     if (o.precision == MPPI_PREC_BF16_MLP && o.block_threads % 64 != 0) return MPPI_ERR_INVALID_ARG;
     // the tcgen05 MLP kernel (rollout_variant 2) has one shape (384 threads per
@@ -427,7 +419,6 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     }
     c->plan.rollout_smem =
         c->plan.variant == mppi::kVariantQuadGroup ? mppi::quad_group_smem_bytes(*c)
-        : c->plan.variant == mppi::kVariantQuadSplit ? mppi::quad_split_smem_bytes(*c, c->plan.rollout_threads)
         : c->plan.variant == mppi::kVariantQuadPair ? mppi::quad_pair_smem_bytes(*c, c->plan.rollout_threads)
         : c->plan.variant == mppi::kVariantMlpBf16 ? mppi::mlp_bf16_smem_bytes(*c, c->plan.rollout_threads)
         : c->plan.variant == mppi::kVariantMlpTc ? mppi::mlp_tc_smem_bytes(*c)
@@ -442,7 +433,6 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     }
     if ((e = mppi::rollout_prepare(*c)) != cudaSuccess ||
         (c->plan.variant == mppi::kVariantQuadGroup && (e = mppi::quad_group_prepare(*c)) != cudaSuccess) ||
-        (c->plan.variant == mppi::kVariantQuadSplit && (e = mppi::quad_split_prepare(*c)) != cudaSuccess) ||
         (c->plan.variant == mppi::kVariantQuadPair && (e = mppi::quad_pair_prepare(*c)) != cudaSuccess) ||
         (c->plan.variant == mppi::kVariantMlpBf16 && (e = mppi::mlp_bf16_prepare(*c)) != cudaSuccess) ||
         (c->plan.variant == mppi::kVariantMlpTc && (e = mppi::mlp_tc_prepare(*c)) != cudaSuccess) ||
@@ -489,7 +479,6 @@ mppi_status mppi_step(mppi_ctx *ctx, const float *x0_d, const float *u_nom_d, fl
         {
             ProfScope ps(ctx, MPPI_PROF_ROLLOUT);
             e = ctx->plan.variant == mppi::kVariantQuadGroup ? mppi::launch_quad_group(*ctx, p)
-                : ctx->plan.variant == mppi::kVariantQuadSplit ? mppi::launch_quad_split(*ctx, p)
                 : ctx->plan.variant == mppi::kVariantQuadPair ? mppi::launch_quad_pair(*ctx, p)
                 : ctx->plan.variant == mppi::kVariantMlpBf16 ? mppi::launch_mlp_bf16(*ctx, p)
                 : ctx->plan.variant == mppi::kVariantMlpTc ? mppi::launch_mlp_tc(*ctx, p)

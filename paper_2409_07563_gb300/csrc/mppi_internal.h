@@ -70,7 +70,6 @@ struct StepParams {
 enum RolloutVariant {
     kVariantGeneric = 1,
     kVariantQuadGroup = 2,
-    kVariantQuadSplit = 3,
     kVariantQuadPair = 4,
     kVariantMlpBf16 = 5,
     kVariantMlpF32 = 6,
@@ -159,10 +158,6 @@ bool quad_group_applicable(const mppi_ctx &c);
 size_t quad_group_smem_bytes(const mppi_ctx &c);
 cudaError_t quad_group_prepare(const mppi_ctx &c);
 cudaError_t launch_quad_group(const mppi_ctx &c, const StepParams &p);
-// rollout_quad_split.cu: a dynamics warp and a cost warp per eight samples
-size_t quad_split_smem_bytes(const mppi_ctx &c, int threads);
-cudaError_t quad_split_prepare(const mppi_ctx &c);
-cudaError_t launch_quad_split(const mppi_ctx &c, const StepParams &p);
 // rollout_quad_pair.cu: one sample per thread, dynamics / cost / crash warps per 32 samples
 bool quad_pair_applicable(const mppi_ctx &c);
 int quad_pair_roles(const mppi_ctx &c);  // warps per 32 samples (4)
