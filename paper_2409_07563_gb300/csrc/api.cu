@@ -359,6 +359,7 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     c->sigma.assign(sigma, sigma + nu);
     c->dyn_params_h.assign(dyn->params, dyn->params + dyn->n_params);
     c->cost_params_h.assign(cost->params, cost->params + cost->n_params);
+    if (c->dyn_kind == MPPI_DYN_QUADROTOR) mppi::quad_pair_order_spheres(*c);
 
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -582,6 +583,7 @@ mppi_status mppi_set_params(mppi_ctx *ctx, const float *dyn_params, const float 
         if (ctx->cost_kind == MPPI_COST_QUAD_OBSTACLES && cost_params[31] != ctx->cost_params_h[31])
             return fail(ctx, MPPI_ERR_INVALID_ARG, "the obstacle count cannot change");
         ctx->cost_params_h.assign(cost_params, cost_params + ctx->cost_params_h.size());
+        if (ctx->dyn_kind == MPPI_DYN_QUADROTOR) mppi::quad_pair_order_spheres(*ctx);
         e = cudaMemcpy(ctx->d_cost, ctx->cost_params_h.data(),
                        ctx->cost_params_h.size() * sizeof(float), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "parameter upload");

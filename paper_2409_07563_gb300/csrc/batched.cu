@@ -52,8 +52,9 @@ constexpr int kBatchRed = 64;  // reduction scratch floats
 // shared memory of the quadrotor warp groups: spheres (kPairSpheres float4)
 // then kPairGroupFloats per group of four warps
 constexpr int kBatchPairFixed = 4 * kPairSpheres;
-static_assert(sizeof(QuadPairConst) <= sizeof(float) * kQuadSmemCostFloats,
-              "the cost slot holds a QuadPairConst");
+// floats of the per-instance cost slot (a QuadPairConst for warp-role tiles)
+constexpr int kBatchCostFloats =
+    kQuadSmemCostFloats > kPairConstFloats ? kQuadSmemCostFloats : kPairConstFloats;
 
 int batch_pair_floats(int threads) {
     return threads >= 128 ? kBatchPairFixed + (threads / 128) * kPairGroupFloats : 0;
@@ -250,10 +251,14 @@ __global__ void __launch_bounds__(256, 2) batch_rollout_kernel(const DevInst *in
             const PairArgs a{I.T, I.dt, I.lam_beta, I.sigma, I.ivar, I.x0, s_u, s_dyn, nk};
             const uint32_t first_k = static_cast<uint32_t>(item.tile * (nt / 4) + group * kWarp);
             float *sg = s_groups + group * kPairGroupFloats;
+            // every sphere pair at every step: listing the near pairs measured
+            // no faster in this kernel (held to 128 registers)
+            constexpr int kL = 0;
             const float tot =
-                I.obstacles
-                    ? pair_group_cost<true, true>(a, *s_const, s_obs, sg, first_k, role, group, lane)
-                    : pair_group_cost<false, true>(a, *s_const, s_obs, sg, first_k, role, group, lane);
+                I.obstacles ? pair_group_cost<true, kL>(a, *s_const, s_obs, s_const->one, sg,
+                                                        first_k, role, group, lane)
+                            : pair_group_cost<false, kL>(a, *s_const, s_obs, s_const->one, sg,
+                                                         first_k, role, group, lane);
             const int k = static_cast<int>(first_k) + lane;
             if (role == 3 && k < I.K) {
                 S = tot;
@@ -589,7 +594,7 @@ mppi_status mppi_batch_create(int n, const mppi_instance_desc *desc, const mppi_
     if (!b) return MPPI_ERR_OOM;
     b->n = n;
     size_t n_params = 0, n_f = 0, n_nz = 0;
-    int max_tu = 1, max_cost = mppi::kQuadSmemCostFloats;
+    int max_tu = 1, max_cost = mppi::kBatchCostFloats;
     for (int i = 0; i < n; ++i) {
         const mppi_instance_desc &d = desc[i];
         HostInst h;

@@ -103,6 +103,7 @@ struct mppi_ctx {
     float dt = 0.f, lambda = 1.f;
     uint64_t seed = 0;
     std::vector<float> sigma, dyn_params_h, cost_params_h;
+    std::vector<int> sphere_order;      // quadrotor crash test: neighbouring spheres paired
     float *d_dyn = nullptr, *d_cost = nullptr, *d_map = nullptr;
     int map_h = 0, map_w = 0;
     mppi::Scratch scr;
@@ -161,6 +162,8 @@ cudaError_t launch_quad_group(const mppi_ctx &c, const StepParams &p);
 // rollout_quad_pair.cu: one sample per thread, dynamics / cost / crash warps per 32 samples
 bool quad_pair_applicable(const mppi_ctx &c);
 int quad_pair_roles(const mppi_ctx &c);  // warps per 32 samples (4)
+bool quad_pair_low_reg(const mppi_ctx &c);
+void quad_pair_order_spheres(mppi_ctx &c);  // after every change of the cost parameters
 size_t quad_pair_smem_bytes(const mppi_ctx &c, int threads);
 cudaError_t quad_pair_prepare(const mppi_ctx &c);
 cudaError_t launch_quad_pair(const mppi_ctx &c, const StepParams &p);

@@ -18,7 +18,22 @@ struct QuadPairConst {
     float s_term, c_crash;
     // sphere pairs (2j, 2j+1): a = (cx, cx', cy, cy'), b = (cz, cz', -r^2, -r'^2)
     float4 sa[kPairSpheres / 2], sb[kPairSpheres / 2];
+    // the same spheres one by one: (cx, cy, cz, -r^2); padding (0, 0, 0, 3e38)
+    float4 one[kPairSpheres];
 };
+constexpr int kPairConstFloats = static_cast<int>(sizeof(QuadPairConst) / sizeof(float));
+// Up to this many sphere pairs near a warp's positions, the cost warp tests
+// only those (held in registers over a ring half); above, every pair.  The
+// single-instance build held to 128 registers (two blocks per SM) lists
+// fewer; a limit of 0 tests every pair at every step.
+constexpr int kPairListedMax = 6;
+constexpr int kLowRegPairListedMax = 4;
+
+// Warp role by warp slot (slot = warp / groups per block), one nibble each:
+// dynamics (0), noise channels 0-1 (1), noise channels 2-3 (2), cost (3).
+// (Measured on GB300 at K = 8192: pairing each dynamics warp with a cost warp
+// on one sub-partition, and the noise warps with each other, was slower.)
+constexpr unsigned kPairRoleOrder = 0x3210u;
 
 constexpr int kPairH = 4;  // steps per ring half (whole Philox blocks of four steps)
 static_assert(kPairH % 4 == 0, "a ring half holds whole noise blocks");
@@ -29,11 +44,23 @@ __device__ __forceinline__ void group_sync(int id, int threads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
-// fma(dz,dz, fma(dy,dy, fma(dx,dx, -r^2))) < 0 for any sphere, with
-// dx = fl(px - cx): one rounding per operation, two spheres per instruction.
-// The sphere pairs come from the kernel parameter (the compiler keeps them in
-// registers across the steps) or, for the low-register build, from shared
-// memory (obs2: sa[j] at 2j, sb[j] at 2j + 1).
+// fma(dz,dz, fma(dy,dy, fma(dx,dx, -r^2))) < 0 for a sphere pair (a, b) as
+// laid out in QuadPairConst::sa/sb, with dx = fl(px - cx): one rounding per
+// operation, two spheres per instruction.
+__device__ __forceinline__ bool crash_pair(unsigned long long X, unsigned long long Y,
+                                           unsigned long long Z, const float4 &a,
+                                           const float4 &b) {
+    const unsigned long long dx = sub2(X, pack2(a.x, a.y));
+    const unsigned long long dy = sub2(Y, pack2(a.z, a.w));
+    const unsigned long long dz = sub2(Z, pack2(b.x, b.y));
+    unsigned long long m = fma2(dx, dx, pack2(b.z, b.w));
+    m = fma2(dy, dy, m);
+    m = fma2(dz, dz, m);
+    float m0, m1;
+    unpack2(m, m0, m1);
+    return (m0 < 0.0f) | (m1 < 0.0f);
+}
+
 __device__ __forceinline__ float4 lds_v4_each_time(const float4 *a) {
     float4 r;
     asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
@@ -42,28 +69,62 @@ __device__ __forceinline__ float4 lds_v4_each_time(const float4 *a) {
     return r;
 }
 
-template <bool kSmemSpheres>
-__device__ __forceinline__ bool crash_any(const QuadPairConst &c, const float4 *obs2, float px,
-                                          float py, float pz) {
+// The crash test against every sphere pair (obs2: sa[j] at 2j, sb[j] at
+// 2j + 1 in shared memory, read at every call: otherwise the loop-invariant
+// loads are hoisted into 128 registers).
+__device__ __forceinline__ bool crash_any(const float4 *obs2, float px, float py, float pz) {
     const unsigned long long X = pack2(px, px), Y = pack2(py, py), Z = pack2(pz, pz);
     bool hit = false;
 #pragma unroll
-    for (int j = 0; j < kPairSpheres / 2; ++j) {
-        // (a volatile load per step: otherwise the loop-invariant loads are
-        // hoisted into 128 registers, which is what this build avoids)
-        const float4 a = kSmemSpheres ? lds_v4_each_time(obs2 + 2 * j) : c.sa[j];
-        const float4 b = kSmemSpheres ? lds_v4_each_time(obs2 + 2 * j + 1) : c.sb[j];
-        const unsigned long long dx = sub2(X, pack2(a.x, a.y));
-        const unsigned long long dy = sub2(Y, pack2(a.z, a.w));
-        const unsigned long long dz = sub2(Z, pack2(b.x, b.y));
-        unsigned long long m = fma2(dx, dx, pack2(b.z, b.w));
-        m = fma2(dy, dy, m);
-        m = fma2(dz, dz, m);
-        float m0, m1;
-        unpack2(m, m0, m1);
-        hit |= (m0 < 0.0f) | (m1 < 0.0f);
-    }
+    for (int j = 0; j < kPairSpheres / 2; ++j)
+        hit |= crash_pair(X, Y, Z, lds_v4_each_time(obs2 + 2 * j), lds_v4_each_time(obs2 + 2 * j + 1));
     return hit;
+}
+
+// Signed-integer key with the order of the floats (for redux.sync).
+__device__ __forceinline__ int float_order_key(float f) {
+    const int b = __float_as_int(f);
+    return b >= 0 ? b : b ^ 0x7fffffff;
+}
+__device__ __forceinline__ float order_key_float(int k) {
+    return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff);
+}
+
+// The spheres that some position of this warp's nx states (ring slots xb,
+// 4 kWarp float4 apart) may lie in: the warp's bounding box of the positions,
+// then lane j tests sphere j (s_one: the spheres one by one, shared memory)
+// against the box.  The test is conservative for
+// the FP32 point test of crash_any: a point that test puts inside a sphere is
+// within (1 + 6e-7) r^2 of its centre, and the box distance, computed with a
+// few roundings, is then below 1.001 r^2 + 1e-6.  Padding spheres (-r^2 =
+// 3e38) are never listed; NaN positions are left out of the box (fminf), and
+// their point test is false either way.  Warp-uniform result.
+__device__ __forceinline__ unsigned near_spheres(const float4 *s_one, const float4 *xb, int nx,
+                                                 int lane) {
+    const float inf = __int_as_float(0x7f800000);
+    float lx = inf, ly = inf, lz = inf, hx = -inf, hy = -inf, hz = -inf;
+    for (int s = 0; s < nx; ++s) {
+        const float4 a = xb[s * 4 * kWarp];
+        lx = fminf(lx, a.x);
+        ly = fminf(ly, a.y);
+        lz = fminf(lz, a.z);
+        hx = fmaxf(hx, a.x);
+        hy = fmaxf(hy, a.y);
+        hz = fmaxf(hz, a.z);
+    }
+    const unsigned all = 0xffffffffu;
+    lx = order_key_float(__reduce_min_sync(all, float_order_key(lx)));
+    ly = order_key_float(__reduce_min_sync(all, float_order_key(ly)));
+    lz = order_key_float(__reduce_min_sync(all, float_order_key(lz)));
+    hx = order_key_float(__reduce_max_sync(all, float_order_key(hx)));
+    hy = order_key_float(__reduce_max_sync(all, float_order_key(hy)));
+    hz = order_key_float(__reduce_max_sync(all, float_order_key(hz)));
+    const float4 o = s_one[lane];
+    const float dx = fmaxf(fmaxf(lx - o.x, o.x - hx), 0.f);
+    const float dy = fmaxf(fmaxf(ly - o.y, o.y - hy), 0.f);
+    const float dz = fmaxf(fmaxf(lz - o.z, o.z - hz), 0.f);
+    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    return __ballot_sync(all, d2 < fmaf(-1.001f, o.w, 1e-6f));
 }
 
 __device__ __forceinline__ float quad_state_cost(const QuadPairConst &c, const float y[13]) {
@@ -284,30 +345,71 @@ __device__ __forceinline__ FloatPair pair_noise(const PairArgs &p, const QuadPai
 
 // Cost warp: state part of the running cost of every x_{t+1}, crash cost,
 // terminal cost.
-template <bool kObstacles, bool kSmemSpheres>
+template <bool kObstacles, int kListed>
 __device__ __forceinline__ FloatPair pair_state_cost(const PairArgs &p, const QuadPairConst &c,
-                                                     const float4 *obs2, const float4 *ring_x,
-                                                     int lane, int nh, int bar_id) {
+                                                     const float4 *obs2, const float4 *s_one,
+                                                     const float4 *ring_x, int lane, int nh,
+                                                     int bar_id) {
     const int T = p.T;
     CompSum J;
-    auto state = [&](const float4 *slot, int t) {
+    // crash test of every sphere pair (all) or of the n listed pairs (la, lb)
+    auto state = [&](const float4 *slot, int t, bool all, int n, const float4 *la,
+                     const float4 *lb) {
         const float4 a = slot[0], b = slot[kWarp], d = slot[2 * kWarp], e = slot[3 * kWarp];
         const float y[13] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, d.x, d.y, d.z, d.w, e.x};
         const float cs = quad_state_cost(c, y);
         float r = cs;
-        if (kObstacles && crash_any<kSmemSpheres>(c, obs2, y[0], y[1], y[2])) r += c.c_crash;
+        if (kObstacles) {
+            bool hit = false;
+            if (all) {
+                hit = crash_any(obs2, y[0], y[1], y[2]);
+            } else {
+                const unsigned long long X = pack2(y[0], y[0]), Y = pack2(y[1], y[1]),
+                                         Z = pack2(y[2], y[2]);
+#pragma unroll
+                for (int i = 0; i < kListed; ++i) {
+                    if (i >= n) break;  // warp-uniform
+                    hit |= crash_pair(X, Y, Z, la[i], lb[i]);
+                }
+            }
+            if (hit) r += c.c_crash;
+        }
         J.add(fmaf(t == T - 1 ? c.s_term : 0.f, cs, r));
     };
     auto states = [&](int hs) {
         const float4 *xb = ring_x + (hs & 1) * kPairH * 4 * kWarp + lane;
         const int nx = min(kPairH, T - hs * kPairH);
-        if (!kSmemSpheres && nx == kPairH) {  // straight-line steady state
+        // the sphere pairs with a sphere near this warp's positions of the
+        // half (warp-uniform), gathered into registers
+        unsigned pm = 0u;
+        if (kObstacles && kListed > 0) {
+            const unsigned near = near_spheres(s_one, xb, nx, lane);
+            pm = (near | (near >> 1)) & 0x55555555u;  // bit 2j: pair j
+        }
+        const int n = __popc(pm);
+        if (kObstacles && (kListed == 0 || n > kListed)) {
+#pragma unroll 1
+            for (int s = 0; s < nx; ++s)
+                state(xb + s * 4 * kWarp, hs * kPairH + s, true, 0, nullptr, nullptr);
+            return;
+        }
+        float4 la[kListed > 0 ? kListed : 1], lb[kListed > 0 ? kListed : 1];
 #pragma unroll
-            for (int s = 0; s < kPairH; ++s) state(xb + s * 4 * kWarp, hs * kPairH + s);
+        for (int i = 0; i < kListed; ++i) {
+            if (i >= n) break;
+            const int j = (__ffs(pm) - 1) >> 1;
+            pm &= pm - 1u;
+            la[i] = obs2[2 * j];
+            lb[i] = obs2[2 * j + 1];
+        }
+        if (nx == kPairH) {  // straight-line steady state
+#pragma unroll
+            for (int s = 0; s < kPairH; ++s)
+                state(xb + s * 4 * kWarp, hs * kPairH + s, false, n, la, lb);
             return;
         }
 #pragma unroll 1
-        for (int s = 0; s < nx; ++s) state(xb + s * 4 * kWarp, hs * kPairH + s);
+        for (int s = 0; s < nx; ++s) state(xb + s * 4 * kWarp, hs * kPairH + s, false, n, la, lb);
     };
     group_sync(bar_id, 4 * kWarp);
     for (int hh = 0; hh < nh; ++hh) {
@@ -320,14 +422,16 @@ __device__ __forceinline__ FloatPair pair_state_cost(const PairArgs &p, const Qu
 
 // One group of 32 samples (first_k, ..., first_k + 31) on warps
 // (role * G + group) of the calling block, role 0 dynamics, 1-2 noise, 3 cost;
-// every thread of the block calls it.  s_group: kPairGroupFloats of shared
-// memory for this group; s_obs: the spheres in shared memory (kSmemSpheres).
+// every thread of the group's four warps calls it.  s_group: kPairGroupFloats
+// of shared memory for this group; s_obs: the sphere pairs in shared memory
+// (sa[j] at 2j, sb[j] at 2j + 1); s_one: the spheres one by one in shared
+// memory.
 // Returns the trajectory cost in the cost warp's threads, +inf elsewhere.
-template <bool kObstacles, bool kSmemSpheres>
+template <bool kObstacles, int kListed = kPairListedMax>
 __device__ __forceinline__ float pair_group_cost(const PairArgs &a, const QuadPairConst &c,
-                                                 const float4 *s_obs, float *s_group,
-                                                 uint32_t first_k, int role, int group,
-                                                 int lane) {
+                                                 const float4 *s_obs, const float4 *s_one,
+                                                 float *s_group, uint32_t first_k, int role,
+                                                 int group, int lane) {
     float4 *ring_x = reinterpret_cast<float4 *>(s_group);
     float4 *ring_v = ring_x + kRingXPair;
     FloatPair *s_part = reinterpret_cast<FloatPair *>(ring_v + kRingVPair);
@@ -340,8 +444,8 @@ __device__ __forceinline__ float pair_group_cost(const PairArgs &a, const QuadPa
         s_part[(role - 1) * kWarp + lane] =
             pair_noise(a, c, ring_v, first_k + lane, 2 * (role - 1), lane, nh, bar_id);
     } else {
-        FloatPair tot = pair_state_cost<kObstacles, kSmemSpheres>(a, c, s_obs, ring_x, lane, nh,
-                                                                 bar_id);
+        FloatPair tot = pair_state_cost<kObstacles, kListed>(a, c, s_obs, s_one, ring_x,
+                                                                 lane, nh, bar_id);
         group_sync(bar_id, 4 * kWarp);  // the noise warps' sums are in place
         tot = pair_add(tot, s_part[lane]);
         tot = pair_add(tot, s_part[kWarp + lane]);
@@ -384,6 +488,8 @@ __device__ inline void pair_const_from_raw(const float *raw, bool obstacles, Qua
         }
         c->sa[j] = make_float4(q[0][0], q[1][0], q[0][1], q[1][1]);
         c->sb[j] = make_float4(q[0][2], q[1][2], q[0][3], q[1][3]);
+        c->one[2 * j] = make_float4(q[0][0], q[0][1], q[0][2], q[0][3]);
+        c->one[2 * j + 1] = make_float4(q[1][0], q[1][1], q[1][2], q[1][3]);
     }
 }
 

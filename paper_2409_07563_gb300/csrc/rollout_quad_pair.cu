@@ -40,31 +40,38 @@ namespace mppi {
 
 namespace {
 
-// Block = G groups of 32 samples: warps [0, G) integrate, [G, 3G) draw
-// the noise (channels 0-1, then 2-3), [3G, 4G) score; group j synchronises
-// on named barrier 1 + j.  kSmemSpheres: the low-register build for large K
-// (two blocks per SM), which reads the spheres from shared memory.
-template <bool kObstacles, bool kSmemSpheres>
-__global__ void __launch_bounds__(256, kSmemSpheres ? 2 : 0)
+// Block = G groups of 32 samples on 4G warps; group j synchronises on named
+// barrier 1 + j.  A block's warp w runs on SM sub-partition w mod 4, so with
+// two groups the warps are ordered (dynamics, noise 0-1, cost, noise 2-3) x
+// (group 0, group 1): each sub-partition holds a dynamics and a cost warp, or
+// two noise warps, which balances their instruction counts.  One group: warps
+// 0-3 in role order.  kLowReg: the build for large K, held to 128 registers
+// so that two blocks share an SM.  The spheres are staged in shared memory
+// (one by one, and in pairs).
+template <bool kObstacles, bool kLowReg>
+__global__ void __launch_bounds__(256, kLowReg ? 2 : 1)
     quad_pair_kernel(const StepParams p, const QuadPairConst c) {
     extern __shared__ __align__(16) float smem[];
     const int T = p.T;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int ngroups = nt / (4 * kWarp);
     const int warp = tid / kWarp, lane = tid % kWarp;
-    const int role = warp / ngroups, group = warp % ngroups;
+    // role of warp slot warp / G, one nibble each: 0, 1, 3, 2
+    const int role = static_cast<int>((kPairRoleOrder >> (4 * (warp / ngroups))) & 0xfu);
+    const int group = warp % ngroups;
     float *s_u = smem + ngroups * kPairGroupFloats;
     float *s_dyn = s_u + round_up4(4 * T);
     float *s_red = s_dyn + 8;
-    float4 *s_obs = reinterpret_cast<float4 *>(s_red + kRedFloats);  // kPairSpheres float4
+    float4 *s_one = reinterpret_cast<float4 *>(s_red + kRedFloats);  // kPairSpheres float4
+    float4 *s_obs = s_one + kPairSpheres;                            // kPairSpheres float4
     // the model parameters are context-owned and constant between steps:
     // staged before the dependency wait; the step's inputs after it
     QuadrotorDyn::prepare(p.dyn_params, s_dyn, tid, nt);
-    if (kSmemSpheres)
-        for (int j = tid; j < kPairSpheres / 2; j += nt) {
-            s_obs[2 * j] = c.sa[j];
-            s_obs[2 * j + 1] = c.sb[j];
-        }
+    for (int j = tid; j < kPairSpheres; j += nt) s_one[j] = c.one[j];
+    for (int j = tid; j < kPairSpheres / 2; j += nt) {
+        s_obs[2 * j] = c.sa[j];
+        s_obs[2 * j + 1] = c.sb[j];
+    }
     wait_for_predecessor();
     for (int i = tid; i < 4 * T; i += nt) s_u[i] = p.u_nom[i];
     __syncthreads();
@@ -72,8 +79,9 @@ __global__ void __launch_bounds__(256, kSmemSpheres ? 2 : 0)
     const PairArgs a{T, p.dt, p.lam_beta, p.sigma, p.ivar, p.x0, s_u, s_dyn,
                      make_noise_key(p.seed, *p.counter)};
     const uint32_t first_k = static_cast<uint32_t>((blockIdx.x * ngroups + group) * kWarp);
-    const float tot = pair_group_cost<kObstacles, kSmemSpheres>(
-        a, c, s_obs, smem + group * kPairGroupFloats, first_k, role, group, lane);
+    constexpr int kListed = kLowReg ? kLowRegPairListedMax : kPairListedMax;
+    const float tot = pair_group_cost<kObstacles, kListed>(
+        a, c, s_obs, s_one, smem + group * kPairGroupFloats, first_k, role, group, lane);
     const int k = static_cast<int>(first_k) + lane;
     float S = __int_as_float(0x7f800000);
     int k_out = -1;
@@ -97,9 +105,9 @@ bool quad_pair_applicable(const mppi_ctx &c) {
 int quad_pair_roles(const mppi_ctx &) { return 4; }
 
 size_t quad_pair_smem_bytes(const mppi_ctx &c, int threads) {
-    const int groups = threads / (quad_pair_roles(c) * kWarp);
+    const int groups = threads / 128;
     return sizeof(float) * (static_cast<size_t>(groups) * kPairGroupFloats + round_up4(4 * c.T) +
-                            8 + kRedFloats + 4 * kPairSpheres);
+                            8 + kRedFloats + 2 * 4 * kPairSpheres);
 }
 
 // The low-register build (spheres in shared memory, two blocks per SM) once
@@ -108,6 +116,42 @@ size_t quad_pair_smem_bytes(const mppi_ctx &c, int threads) {
 bool quad_pair_low_reg(const mppi_ctx &c) {
     const long groups = (static_cast<long>(c.K) + kWarp - 1) / kWarp;
     return groups > 2L * c.num_sms;
+}
+
+// The crash test takes the spheres two per instruction and, for each ring
+// half, only the pairs with a sphere near the warp's positions: pairing
+// neighbouring spheres lists fewer pairs.  Greedy: each sphere not yet paired,
+// in index order, with the nearest unpaired one (centre distance).  The test
+// is an OR over the spheres, so the order changes no decision.
+void quad_pair_order_spheres(mppi_ctx &c) {
+    c.sphere_order.clear();
+    if (c.cost_kind != MPPI_COST_QUAD_OBSTACLES) return;
+    const std::vector<float> &cp = c.cost_params_h;
+    const int n = static_cast<int>(cp[31]);
+    std::vector<bool> used(n, false);
+    for (int i = 0; i < n; ++i) {
+        if (used[i]) continue;
+        used[i] = true;
+        c.sphere_order.push_back(i);
+        int best = -1;
+        float bd = 0.f;
+        for (int j = 0; j < n; ++j) {
+            if (used[j]) continue;
+            float d = 0.f;
+            for (int a = 0; a < 3; ++a) {
+                const float e = cp[33 + 4 * i + a] - cp[33 + 4 * j + a];
+                d += e * e;
+            }
+            if (best < 0 || d < bd) {
+                best = j;
+                bd = d;
+            }
+        }
+        if (best >= 0) {
+            used[best] = true;
+            c.sphere_order.push_back(best);
+        }
+    }
 }
 
 cudaError_t quad_pair_prepare(const mppi_ctx &c) {
@@ -138,11 +182,12 @@ cudaError_t launch_quad_pair(const mppi_ctx &c, const StepParams &p) {
     const bool obstacles = c.cost_kind == MPPI_COST_QUAD_OBSTACLES;
     const int n = obstacles ? static_cast<int>(cp[31]) : 0;
     k.c_crash = obstacles ? cp[32] : 0.f;
+    const bool ordered = static_cast<int>(c.sphere_order.size()) == n;
     for (int j = 0; j < kPairSpheres / 2; ++j) {
         float q[2][4];
         for (int h = 0; h < 2; ++h) {
-            const int i = 2 * j + h;
-            if (i < n) {
+            const int i = 2 * j + h < n && ordered ? c.sphere_order[2 * j + h] : 2 * j + h;
+            if (2 * j + h < n) {
                 const float r = cp[33 + 4 * i + 3];
                 q[h][0] = cp[33 + 4 * i];
                 q[h][1] = cp[33 + 4 * i + 1];
@@ -155,6 +200,8 @@ cudaError_t launch_quad_pair(const mppi_ctx &c, const StepParams &p) {
         }
         k.sa[j] = make_float4(q[0][0], q[1][0], q[0][1], q[1][1]);
         k.sb[j] = make_float4(q[0][2], q[1][2], q[0][3], q[1][3]);
+        k.one[2 * j] = make_float4(q[0][0], q[0][1], q[0][2], q[0][3]);
+        k.one[2 * j + 1] = make_float4(q[1][0], q[1][1], q[1][2], q[1][3]);
     }
     cudaLaunchAttribute attr[1];
     const cudaLaunchConfig_t cfg = pdl_config(dim3(c.plan.rollout_blocks),

@@ -131,6 +131,25 @@ def test_noise_bits_exact_and_normals(m, seed, step):
             assert np.all(np.abs(gz[k, q] - oz) <= 8 * ulp + 2.0**-22), (k, q, gz[k, q], oz)
 
 
+def test_normals_two_million_against_the_oracle(m):
+    """Every normal of 8192 samples x 64 Philox blocks (2,097,152 normals, about
+    an eighth of the 2^24 uniforms of the radius) against the oracle's FP64
+    Box-Muller of the same bits: the kernels' logf, square root (one Newton
+    step on rsqrtf) and sincospif stay within the normals' bound."""
+    K, Q = 8192, 64
+    bits = torch.empty(K * Q * 4, dtype=torch.int32, device="cuda")
+    z = torch.empty(K * Q * 4, dtype=torch.float32, device="cuda")
+    m.mppi_sample_noise(11, 5, K, Q, bits, z)
+    torch.cuda.synchronize()
+    gz = z.cpu().numpy().astype(np.float64).reshape(K, Q * 4)
+    oz = oracle.normals(11, 5, K, 4 * Q, 1)[:, :, 0]      # nu = 1: block q holds t = 4q..4q+3
+    ulp = np.spacing(np.abs(oz).astype(np.float32)).astype(np.float64)
+    err = np.abs(gz - oz)
+    print(f"max |dz| = {(err / ulp).max():.2f} ulp(|z|); max |dz| - 2^-22 allowance "
+          f"{(np.maximum(err - 2.0**-22, 0) / ulp).max():.2f} ulp")
+    assert np.all(err <= 8 * ulp + 2.0**-22)
+
+
 # --------------------------------------------------------------------------
 # the three single-instance workloads at full size
 # --------------------------------------------------------------------------
@@ -192,6 +211,24 @@ def test_quadrotor_one_lane_warp_groups_large_k(m):
     # memory (two blocks per SM); checked at rows the oracle computes alone
     p = as_f32_problem(W.quadrotor(K=40000, T=20, lam=300.0, beta=0))
     g, _ = run_gpu(m, p, rollout_variant=4)
+    compare(p, g)
+
+
+@pytest.mark.parametrize("n_obs,box,K", [(32, 2.0, 2048), (32, 2.0, 40000), (7, 3.0, 1001),
+                                         (31, 6.0, 4096), (1, 1.0, 640)])
+def test_quadrotor_crash_test_listed_spheres(m, n_obs, box, K):
+    """The cost warp tests only the sphere pairs near its warp's positions of
+    each four-step half, or every pair when more than the listed limit are
+    near.  Spheres packed around the start (most halves over the limit),
+    spread ones (few listed), odd counts (padding), one sphere; the register
+    build (K = 2048, 4096) and the 128-register build (K = 40000); every
+    sample's cost and the update against the oracle, with crash decisions
+    allowed to differ only within the FP32 bound of the boundary."""
+    rng = np.random.default_rng(400 + n_obs)
+    obs = np.column_stack([rng.uniform(-box, box, (n_obs, 3)), rng.uniform(0.3, 0.8, n_obs)])
+    p = as_f32_problem(W.quadrotor(K=K, T=48, lam=300.0, beta=0, obstacles=obs))
+    g, _ = run_gpu(m, p)
+    assert g["status"] == 0
     compare(p, g)
 
 
