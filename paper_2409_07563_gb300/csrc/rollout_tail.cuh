@@ -32,6 +32,21 @@ constexpr float kCandidateSpan = 110.f;
 // Candidates per last-block thread beyond which the last block leaves the
 // update to the update kernel, which then scans every sample.
 constexpr int kListPerThread = 8;
+// Candidate slots of its block that each merging thread loads with the
+// block's partials.
+constexpr int kSpecCand = 4;
+// Device-scope atomic add with acquire and release semantics: the writes
+// this thread has made or observed (a barrier before it) become visible to
+// whoever reads the result later, and this thread sees theirs.
+__device__ __forceinline__ unsigned int atomic_add_acq_rel(unsigned int *a, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                 : "=r"(old)
+                 : "l"(a), "r"(v)
+                 : "memory");
+    return old;
+}
+
 // Order-preserving unsigned key of a float (for atomicMin on costs).
 __device__ __forceinline__ unsigned int float_key(float f) {
     const unsigned int b = __float_as_uint(f);
@@ -39,6 +54,73 @@ __device__ __forceinline__ unsigned int float_key(float f) {
 }
 __device__ __forceinline__ float key_float(unsigned int k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// End of the merge, every thread of the last block: the inline update when
+// the non-zero list is short (nnz entries in s_nzk / s_nzw), then the
+// statistics and the step bookkeeping.
+__device__ inline void finish_weights(const StepParams &p, bool list_mode, int nnz, bool ok,
+                                      float rho, float eta_v, FloatPair eta2,
+                                      unsigned long long step, const int *s_nzk,
+                                      const float *s_nzw, const float *s_unom) {
+    const float inf = __int_as_float(0x7f800000);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __syncthreads();
+    const int QT = (p.T + 3) / 4, Q = p.nu * QT;
+    const int per_thread = (Q + nt - 1) / nt;
+    // (per_thread >= 1, so an inline list has at most kInlineUpdateCalls entries)
+    // (CEM replaces the weights after this kernel: no inline update then)
+    const bool inline_update =
+        p.n_elite == 0 && list_mode && nnz * per_thread <= kInlineUpdateCalls;
+    if (inline_update) {
+        const NoiseKey nk = make_noise_key(p.seed, step);
+        const float *un = s_unom ? s_unom : p.u_nom;  // the block's shared copy when it has one
+        for (int q = tid; q < Q; q += nt) {
+            const int j = q / QT, t0 = 4 * (q % QT);
+            const float sig = p.sigma[j];
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int idx = 0; idx < nnz; ++idx) {
+                const int k = s_nzk[idx];
+                const float w = s_nzw[idx];
+                float z[4];
+                box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(q)), z);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] += w * (sig * z[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (t0 + i < p.T) {
+                    const int o = (t0 + i) * p.nu + j;
+                    p.u_new[o] = un[o] + p.gamma * acc[i];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const float F = ok ? rho - p.lambda * logf(eta_v / static_cast<float>(p.K)) : inf;
+        const float ess = ok ? eta_v * eta_v / (eta2.hi + eta2.lo) : 0.f;
+        if (!ok) atomicOr(p.status, 1u << MPPI_ERR_NUMERIC);
+        p.scalars[0] = ok ? rho : inf;
+        p.scalars[1] = ok ? eta_v : 0.f;
+        p.scalars[2] = F;
+        p.scalars[3] = ess;
+        p.scalars[4] = ok ? 1.f : 0.f;
+        p.scalars[5] = list_mode ? static_cast<float>(nnz) : -1.f;  // -1: scan every sample
+        p.scalars[6] = inline_update ? 1.f : 0.f;
+        *reinterpret_cast<unsigned int *>(p.scalars + 7) = 0xffffffffu;  // running minimum
+        if (p.stats_out) {
+            p.stats_out[0] = F;
+            p.stats_out[1] = p.scalars[0];
+            p.stats_out[2] = p.scalars[1];
+            p.stats_out[3] = ess;
+        }
+        if (inline_update) {  // the update kernel will find nothing to do
+            *p.last_step = step;
+            *p.counter = step + 1ull;
+        }
+        p.tickets[0] = 0u;  // ready for the next launch
+    }
 }
 
 // Merge of the per-block partials by the last block: rho = min rho_b,
@@ -67,7 +149,19 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, int ca
     const int2 *cand2 = reinterpret_cast<const int2 *>(p.cand);
 
     float4 mine = make_float4(inf, 0.f, 0.f, 0.f);  // (rho_b, eta_b, eta2_b, n_cand_b)
-    if (fast && tid < nblocks) mine = __ldcg(part4 + tid);
+    // with its block's partials each thread loads the block's first candidate
+    // slots in the same round trip (slots past the block's count hold stale
+    // pairs and are not used)
+    int2 spec[kSpecCand];
+#pragma unroll
+    for (int r = 0; r < kSpecCand; ++r) spec[r] = make_int2(0, 0);
+    if (fast && tid < nblocks) {
+        mine = __ldcg(part4 + tid);
+        const int2 *cb = cand2 + static_cast<size_t>(tid) * cand_stride;
+#pragma unroll
+        for (int r = 0; r < kSpecCand; ++r)
+            if (r < cand_stride) spec[r] = __ldcg(cb + r);
+    }
     float rmin = mine.x;
     if (!fast)
         for (int b = tid; b < nblocks; b += nt) rmin = fminf(rmin, __ldcg(p.partials + 4 * b));
@@ -95,6 +189,43 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, int ca
     const float eta_v = eta.hi + eta.lo;
     const bool ok = is_finite(rho) && eta_v > 0.f;
 
+    // every block has at most kSpecCand candidates (the usual case): each
+    // thread lists its block's non-zero weights from the slots it loaded, in
+    // block order = sample order, with no second round trip
+    const int my_cnt = fast && tid < nblocks ? static_cast<int>(mine.w) : 0;
+    const bool few = fast && !__syncthreads_or(my_cnt > kSpecCand);
+    if (few) {
+        float w[kSpecCand];
+        int keep = 0;
+#pragma unroll
+        for (int r = 0; r < kSpecCand; ++r) {
+            w[r] = 0.f;
+            if (ok && r < my_cnt) {
+                w[r] = expf(-(__int_as_float(spec[r].y) - rho) / p.lambda) / eta_v;
+                keep += w[r] != 0.f;
+            }
+        }
+        int nnz_few;
+        int at = block_exclusive_scan(keep, ired, nnz_few);  // contains barriers
+#pragma unroll
+        for (int r = 0; r < kSpecCand; ++r) {
+            if (r < my_cnt && w[r] != 0.f) {
+                if (p.checked && !(at < p.K && spec[r].x >= 0 && spec[r].x < p.K)) {
+                    flag_check(p.status);
+                    continue;
+                }
+                p.nz[at] = spec[r].x;
+                p.w[at] = w[r];
+                if (at < kInlineUpdateCalls) {
+                    s_nzk[at] = spec[r].x;
+                    s_nzw[at] = w[r];
+                }
+                ++at;
+            }
+        }
+        finish_weights(p, true, nnz_few, ok, rho, eta_v, eta2, step, s_nzk, s_nzw, s_unom);
+        return;
+    }
     // candidate counts: one block per thread (fast) or a contiguous range
     const int per = fast ? 1 : (nblocks + nt - 1) / nt;
     const int b_begin = min(nblocks, tid * per);
@@ -213,62 +344,7 @@ __device__ inline void finalize_weights(const StepParams &p, int nblocks, int ca
             }
         }
     }
-    __syncthreads();
-    const int QT = (p.T + 3) / 4, Q = p.nu * QT;
-    const int per_thread = (Q + nt - 1) / nt;
-    // (per_thread >= 1, so an inline list has at most kInlineUpdateCalls entries)
-    // (CEM replaces the weights after this kernel: no inline update then)
-    const bool inline_update =
-        p.n_elite == 0 && list_mode && nnz * per_thread <= kInlineUpdateCalls;
-    if (inline_update) {
-        const NoiseKey nk = make_noise_key(p.seed, step);
-        const float *un = s_unom ? s_unom : p.u_nom;  // the block's shared copy when it has one
-        for (int q = tid; q < Q; q += nt) {
-            const int j = q / QT, t0 = 4 * (q % QT);
-            const float sig = p.sigma[j];
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int idx = 0; idx < nnz; ++idx) {
-                const int k = s_nzk[idx];
-                const float w = s_nzw[idx];
-                float z[4];
-                box_muller(noise_bits(nk, static_cast<uint32_t>(k), static_cast<uint32_t>(q)), z);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) acc[i] += w * (sig * z[i]);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (t0 + i < p.T) {
-                    const int o = (t0 + i) * p.nu + j;
-                    p.u_new[o] = un[o] + p.gamma * acc[i];
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        const float F = ok ? rho - p.lambda * logf(eta_v / static_cast<float>(p.K)) : inf;
-        const float ess = ok ? eta_v * eta_v / (eta2.hi + eta2.lo) : 0.f;
-        if (!ok) atomicOr(p.status, 1u << MPPI_ERR_NUMERIC);
-        p.scalars[0] = ok ? rho : inf;
-        p.scalars[1] = ok ? eta_v : 0.f;
-        p.scalars[2] = F;
-        p.scalars[3] = ess;
-        p.scalars[4] = ok ? 1.f : 0.f;
-        p.scalars[5] = list_mode ? static_cast<float>(nnz) : -1.f;  // -1: scan every sample
-        p.scalars[6] = inline_update ? 1.f : 0.f;
-        *reinterpret_cast<unsigned int *>(p.scalars + 7) = 0xffffffffu;  // running minimum
-        if (p.stats_out) {
-            p.stats_out[0] = F;
-            p.stats_out[1] = p.scalars[0];
-            p.stats_out[2] = p.scalars[1];
-            p.stats_out[3] = ess;
-        }
-        if (inline_update) {  // the update kernel will find nothing to do
-            *p.last_step = step;
-            *p.counter = step + 1ull;
-        }
-        p.tickets[0] = 0u;  // ready for the next launch
-    }
+    finish_weights(p, list_mode, nnz, ok, rho, eta_v, eta2, step, s_nzk, s_nzw, s_unom);
 }
 
 // Called by every thread of the block after its samples are done; S is this
@@ -293,6 +369,9 @@ __device__ inline void block_weight_tail(const StepParams &p, float S, int k, fl
     if (threadIdx.x == 0) {
         float m = rho_b;
         if (is_finite(rho_b)) {
+            // (waited for: pruning against the minimum of the blocks that
+            // finished earlier keeps the candidate lists short; a value read
+            // before the block reductions prunes far less, measured slower)
             const unsigned int old =
                 atomicMin(reinterpret_cast<unsigned int *>(p.scalars + 7), float_key(rho_b));
             m = fminf(rho_b, key_float(old));
@@ -314,22 +393,19 @@ __device__ inline void block_weight_tail(const StepParams &p, float S, int k, fl
     }
     __shared__ bool s_last;
     // the barrier orders every thread's candidate write before thread 0's
-    // device-scope fence (cumulative), and so before the ticket
+    // release (cumulative), and so before the ticket; in the last block, the
+    // barrier after thread 0's acquire orders every thread's reads after it
     __syncthreads();
     if (threadIdx.x == 0) {
         p.partials[4 * blockIdx.x + 0] = rho_b;
         p.partials[4 * blockIdx.x + 1] = eta_b.hi + eta_b.lo;
         p.partials[4 * blockIdx.x + 2] = eta2_b.hi + eta2_b.lo;
         p.partials[4 * blockIdx.x + 3] = static_cast<float>(n_cand);
-        __threadfence();
-        const unsigned int ticket = atomicAdd(p.tickets, 1u);
+        const unsigned int ticket = atomic_add_acq_rel(p.tickets, 1u);
         s_last = (ticket == gridDim.x - 1);
     }
     __syncthreads();
-    if (s_last) {
-        __threadfence();
-        finalize_weights(p, gridDim.x, cand_stride, s_red, s_unom);
-    }
+    if (s_last) finalize_weights(p, gridDim.x, cand_stride, s_red, s_unom);
     allow_successor_launch();
 }
 
