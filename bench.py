@@ -764,6 +764,38 @@ def workload_config(p):
             "l2": "flushed by a 256 MiB write before every timed step"}
 
 
+def profile_form(args):
+    """Steps of the batched (configuration 3) or differentiable (configuration
+    4, forward + adjoint backward) form only, for an ncu capture of their
+    kernels; prints one line, measures nothing."""
+    import torch
+    import paper_2409_07563_gb300 as m
+    m.build()
+    dev = torch.device("cuda", 0)
+    n = args.warmup + args.steps
+    if args.profile_form == "batched":
+        b = m.MPPIBatch(W.batched())
+        for _ in range(n):
+            b.step()
+        torch.cuda.synchronize()
+        b.close()
+    else:
+        p = W.differentiable()
+        ctl = m.MPPI.from_problem(p)
+        x0 = torch.tensor(p["x0"], dtype=torch.float32, device=dev)
+        u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device=dev)
+        tgt = torch.tensor(p["u_target"].reshape(-1), dtype=torch.float32, device=dev)
+        un, g = torch.empty_like(u), torch.empty_like(u)
+        for _ in range(n):
+            ctl.step_into(x0, u, un)
+            torch.mul(torch.sub(un, tgt), 2.0, out=g)
+            ctl.backward(g)
+        torch.cuda.synchronize()
+        ctl.close()
+    print(json.dumps({"profile_form": args.profile_form, "steps": n}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -780,8 +812,13 @@ def main():
                     help="bf16: the bicycle workload's MLP on the tensor cores (diagnostic)")
     ap.add_argument("--rollout-variant", type=int, default=0,
                     help="the context's rollout_variant option (diagnostic)")
+    ap.add_argument("--profile-form", default=None, choices=["batched", "differentiable"],
+                    help="run only --warmup + --steps steps of one extension form and exit "
+                         "(a short program for an ncu capture of its kernels; no timing)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.profile_form:
+        return profile_form(args)
 
     p = make_workload(args.workload, args.K)
     if args.precision == "bf16" and args.workload != "bicycle":
