@@ -22,6 +22,8 @@
 // dL/dS_k is exactly zero (weight underflowed) contribute exactly zero and
 // skip the sweep.  Three kernels: forward sweep (checkpoints, a_k, direct
 // derivatives, k*), reverse sweep (adjoint derivatives), centred reduction.
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "models.cuh"
 #include "mppi_internal.h"
@@ -141,86 +143,120 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_forward_kernel(const AdjP
 
 constexpr int kMaxSeg = 128;  // C = ceil(sqrt T) <= 128 for T <= 16384
 
-// Reverse sweep of every sample with non-zero weight: dS_k/dl, dS_k/dm_c.
-__global__ void __launch_bounds__(kAdjThreads) adjoint_reverse_kernel(const AdjParams a) {
+// Reverse sweep: one warp per sample with non-zero weight (dS_k/dl, dS_k/dm_c).
+// The lanes recompute the checkpoint segments of a window in parallel, each
+// from its checkpoint, and leave per step t the Jacobian entries at
+// (x_t, v_t) and the running-cost gradient 2 Q (x_t - goal) in shared memory;
+// lane 0 then walks the window backwards with multiply-adds only (the
+// adjoint recurrence no longer waits for sincos and divisions).  Windows of
+// whole segments, last first; the arithmetic per step is the serial sweep's.
+constexpr int kRevWarps = 4;      // warps per block
+constexpr int kRevWindow = 240;   // steps held in shared memory per warp
+constexpr int kRevStep = 12;      // floats per step: 8 Jacobian entries, 4 cost-gradient terms
+__global__ void __launch_bounds__(kRevWarps * kWarp) adjoint_reverse_kernel(const AdjParams a) {
     const StepParams &p = a.sp;
     __shared__ float s_par[8];
+    __shared__ float s_step[kRevWarps][kRevWindow * kRevStep];
+    __shared__ float s_xT[kRevWarps][4];
     if (threadIdx.x < 4) s_par[threadIdx.x] = p.dyn_params[threadIdx.x];
     if (threadIdx.x == 0) s_par[4] = 1.0f / p.dyn_params[2];
     __syncthreads();
     const float *C = p.cost_params;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int K = p.K, T = p.T;
+    const int K = p.K, T = p.T, CS = a.C, nck = a.nck;
+    const int lane = threadIdx.x % kWarp, wib = threadIdx.x / kWarp;
+    const int warps = gridDim.x * kRevWarps, gw = blockIdx.x * kRevWarps + wib;
     const NoiseKey nk = make_noise_key(p.seed, *p.last_step);
-    if (k < K) {
-        if (weight_of(p, k) != 0.f) {
-            const float Q[4] = {C[0], C[1], C[2], C[3]};
-            const float gl[4] = {C[5], C[6], C[7], C[8]};
-            const float s_term = C[9], sig = p.sigma[0], dt = p.dt;
-            float xs[kMaxSeg + 1][4];
-            float vs[kMaxSeg];
-            // adjoint at x_T: terminal cost and the last running cost
-            float lam[4];
+    const float Q[4] = {C[0], C[1], C[2], C[3]};
+    const float gl[4] = {C[5], C[6], C[7], C[8]};
+    const float s_term = C[9], sig = p.sigma[0], dt = p.dt;
+    const int wseg = kRevWindow / CS;  // segments per window (>= 1: C <= kMaxSeg < kRevWindow)
+    float *buf = s_step[wib];
+    for (int base = gw * kWarp; base < K; base += warps * kWarp) {
+        const int kl = base + lane;
+        unsigned todo = __ballot_sync(0xffffffffu, kl < K && weight_of(p, kl) != 0.f);
+        while (todo) {  // warp-uniform: one sample at a time
+            const int k = base + __ffs(todo) - 1;
+            todo &= todo - 1u;
+            float lam[4] = {0.f, 0.f, 0.f, 0.f};
             float gl_p = 0.f, gmc = 0.f;
-            bool first = true;
-            for (int c = a.nck - 1; c >= 0; --c) {
-                const int t_begin = c * a.C, t_end = min(T, t_begin + a.C);
-                // recompute the segment's states and controls from its checkpoint
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    xs[0][i] = a.ckpt[(static_cast<size_t>(c) * 4 + i) * K + k];
-                float z[4];
-                for (int t = t_begin; t < t_end; ++t) {
-                    if (t == t_begin || (t & 3) == 0)
-                        box_muller(noise_bits(nk, static_cast<uint32_t>(k), t / 4), z);
-                    const float v = a.u_nom[t] + sig * z[t & 3];
-                    vs[t - t_begin] = v;
-                    float x[4] = {xs[t - t_begin][0], xs[t - t_begin][1], xs[t - t_begin][2],
-                                  xs[t - t_begin][3]};
-                    CartpoleDyn::step(x, &v, s_par, dt);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) xs[t - t_begin + 1][i] = x[i];
-                }
-                if (first) {
-                    const int n = t_end - t_begin;
+            for (int c_end = nck; c_end > 0; c_end -= wseg) {
+                const int c_begin = max(0, c_end - wseg);
+                const int t0 = c_begin * CS, t1 = min(T, c_end * CS);
+                // recompute the window's segments, one per lane
+                for (int c = c_begin + lane; c < c_end; c += kWarp) {
+                    const int t_begin = c * CS, t_end = min(T, t_begin + CS);
+                    float x[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
-                        lam[i] = 2.0f * (1.0f + s_term) * Q[i] * (xs[n][i] - gl[i]);
-                    first = false;
-                }
-                for (int t = t_end - 1; t >= t_begin; --t) {
-                    const int o = t - t_begin;
-                    const CartpoleJac J = cartpole_jac(s_par, xs[o][2], xs[o][3], vs[o]);
-                    // parameter gradient through x_{t+1} = x_t + dt f(x_t, v_t)
-                    gl_p += dt * (lam[1] * J.xdd_l + lam[3] * J.thdd_l);
-                    gmc += dt * (lam[1] * J.xdd_mc + lam[3] * J.thdd_mc);
-                    // lam_t = (I + dt df/dx)^T lam_{t+1}
-                    const float l0 = lam[0], l1 = lam[1], l2 = lam[2], l3 = lam[3];
-                    lam[1] = l1 + dt * l0;
-                    lam[2] = l2 + dt * (l1 * J.xdd_th + l3 * J.thdd_th);
-                    lam[3] = l3 + dt * (l2 + l1 * J.xdd_w + l3 * J.thdd_w);
-                    lam[0] = l0;
-                    if (t >= 1) {  // running cost of step t-1 sits on x_t
+                        x[i] = a.ckpt[(static_cast<size_t>(c) * 4 + i) * K + k];
+                    float z[4];
+                    for (int t = t_begin; t < t_end; ++t) {
+                        if (t == t_begin || (t & 3) == 0)
+                            box_muller(noise_bits(nk, static_cast<uint32_t>(k), t / 4), z);
+                        const float v = a.u_nom[t] + sig * z[t & 3];
+                        const CartpoleJac J = cartpole_jac(s_par, x[2], x[3], v);
+                        float *o = buf + (t - t0) * kRevStep;
+                        o[0] = J.xdd_th;
+                        o[1] = J.xdd_w;
+                        o[2] = J.thdd_th;
+                        o[3] = J.thdd_w;
+                        o[4] = J.xdd_l;
+                        o[5] = J.xdd_mc;
+                        o[6] = J.thdd_l;
+                        o[7] = J.thdd_mc;
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) lam[i] += 2.0f * Q[i] * (xs[o][i] - gl[i]);
+                        for (int i = 0; i < 4; ++i) o[8 + i] = 2.0f * Q[i] * (x[i] - gl[i]);
+                        CartpoleDyn::step(x, &v, s_par, dt);
+                    }
+                    if (c == nck - 1)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) s_xT[wib][i] = x[i];
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    if (c_end == nck)  // adjoint at x_T: terminal cost and the last running cost
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            lam[i] = 2.0f * (1.0f + s_term) * Q[i] * (s_xT[wib][i] - gl[i]);
+                    for (int t = t1 - 1; t >= t0; --t) {
+                        const float *o = buf + (t - t0) * kRevStep;
+                        // parameter gradient through x_{t+1} = x_t + dt f(x_t, v_t)
+                        gl_p += dt * (lam[1] * o[4] + lam[3] * o[6]);
+                        gmc += dt * (lam[1] * o[5] + lam[3] * o[7]);
+                        // lam_t = (I + dt df/dx)^T lam_{t+1}
+                        const float l0 = lam[0], l1 = lam[1], l2 = lam[2], l3 = lam[3];
+                        lam[1] = l1 + dt * l0;
+                        lam[2] = l2 + dt * (l1 * o[0] + l3 * o[2]);
+                        lam[3] = l3 + dt * (l2 + l1 * o[1] + l3 * o[3]);
+                        lam[0] = l0;
+                        if (t >= 1)  // running cost of step t-1 sits on x_t
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) lam[i] += o[8 + i];
                     }
                 }
+                __syncwarp();
             }
-            a.per_sample[6 * K + k] = gl_p;
-            a.per_sample[7 * K + k] = gmc;
+            if (lane == 0) {
+                a.per_sample[6 * K + k] = gl_p;
+                a.per_sample[7 * K + k] = gmc;
+            }
         }
     }
 }
 
 // dL/dtheta = -(1/lambda) [sum w Da Dg - (sum w Da)(sum w Dg)] around k*,
-// block partials merged in a fixed order by the last block.
+// block partials merged in a fixed order by the last block.  The fifteen sums
+// are reduced together: a warp-level tree each, then one shared-memory round.
 __global__ void __launch_bounds__(kAdjThreads) adjoint_reduce_kernel(const AdjParams a) {
     const StepParams &p = a.sp;
-    __shared__ float s_red[64];
+    constexpr int kNw = kAdjThreads / kWarp;
+    __shared__ float s_red[kNw][15][2];
+    __shared__ float s_tot[15];
     __shared__ bool s_last;
     const int K = p.K;
     const int kr = *a.kref;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
     float v[15];
 #pragma unroll
     for (int i = 0; i < 15; ++i) v[i] = 0.f;
@@ -239,9 +275,21 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_reduce_kernel(const AdjPa
     }
 #pragma unroll
     for (int i = 0; i < 15; ++i) {
-        const FloatPair t = block_pair_sum(FloatPair{v[i], 0.f}, s_red);
-        if (threadIdx.x == 0) a.bpart[15 * blockIdx.x + i] = t.hi + t.lo;
+        const FloatPair t = warp_pair_sum(FloatPair{v[i], 0.f});
+        if (lane == 0) {
+            s_red[wid][i][0] = t.hi;
+            s_red[wid][i][1] = t.lo;
+        }
     }
+    __syncthreads();
+    if (threadIdx.x < 15) {
+        FloatPair acc{0.f, 0.f};
+        for (int w = 0; w < kNw; ++w)
+            acc = pair_add(acc, FloatPair{s_red[w][threadIdx.x][0], s_red[w][threadIdx.x][1]});
+        a.bpart[15 * blockIdx.x + threadIdx.x] = acc.hi + acc.lo;
+    }
+    // the barrier orders the partial stores before thread 0's fence and ticket
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         s_last = atomicAdd(p.tickets + 3, 1u) == gridDim.x - 1;
@@ -249,19 +297,20 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_reduce_kernel(const AdjPa
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    float tot[15];
-#pragma unroll
-    for (int i = 0; i < 15; ++i) {
+    // value i on warp i % kNw: lanes take blocks lane, lane + 32, ... then a
+    // warp tree (fixed order)
+    for (int i = wid; i < 15; i += kNw) {
         FloatPair acc{0.f, 0.f};
-        for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += blockDim.x)
+        for (int b = lane; b < static_cast<int>(gridDim.x); b += kWarp)
             acc = pair_add(acc, FloatPair{__ldcg(a.bpart + 15 * b + i), 0.f});
-        const FloatPair t = block_pair_sum(acc, s_red);
-        tot[i] = t.hi + t.lo;
+        acc = warp_pair_sum(acc);
+        if (lane == 0) s_tot[i] = acc.hi + acc.lo;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int i = 0; i < 7; ++i)
-            a.grad_out[i] = (kr < K) ? -(tot[8 + i] - tot[0] * tot[1 + i]) / p.lambda : 0.f;
+            a.grad_out[i] = (kr < K) ? -(s_tot[8 + i] - s_tot[0] * s_tot[1 + i]) / p.lambda : 0.f;
         p.tickets[3] = 0u;
     }
 }
@@ -299,7 +348,11 @@ cudaError_t launch_adjoint(const mppi_ctx &c, const StepParams &sp, const float 
     if (e != cudaSuccess) return e;
     adjoint_forward_kernel<<<blocks, kAdjThreads, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    adjoint_reverse_kernel<<<blocks, kAdjThreads, 0, s>>>(a);
+    // reverse sweep: enough warps to cover K in 32-sample strides, at most
+    // two blocks per SM
+    const int rev_blocks = std::max(1, std::min((c.K + kRevWarps * kWarp - 1) / (kRevWarps * kWarp),
+                                                2 * c.num_sms));
+    adjoint_reverse_kernel<<<rev_blocks, kRevWarps * kWarp, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     adjoint_reduce_kernel<<<blocks, kAdjThreads, 0, s>>>(a);
     return cudaGetLastError();
