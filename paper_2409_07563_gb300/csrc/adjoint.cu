@@ -101,30 +101,65 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_forward_kernel(const AdjP
     const float *C = p.cost_params;  // Q(4), R(1), goal(4), s
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const NoiseKey nk = make_noise_key(p.seed, *p.last_step);
-    const int K = p.K, T = p.T;
+    const int K = p.K, T = p.T, QT = (T + 3) / 4;
     if (k < K) {
         float x[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) x[i] = a.x0[i];
         float dQ[4] = {0.f, 0.f, 0.f, 0.f}, dR = 0.f, ak = 0.f;
         const float sig = p.sigma[0];
-        float z[4];
-        for (int t = 0; t < T; ++t) {
-            if (t % a.C == 0) {
-                const int c = t / a.C;
+        // four-step groups; the next group's normals, nominal controls and
+        // loss gradient are fetched while this group integrates, so Philox,
+        // Box-Muller and the loads stay off the state chain (the block drawn
+        // after the last group is never used)
+        float z[4], u4[4], g4[4];
+        group_normals<1>(nk, static_cast<uint32_t>(k), 0, QT, z);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            u4[s] = s < T ? a.u_nom[s] : 0.f;
+            g4[s] = s < T ? a.G[s] : 0.f;
+        }
+        int to_ckpt = 0, c = 0;  // steps to the next checkpoint (every a.C steps)
+        auto one_step = [&](int s) {
+            if (to_ckpt == 0) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) a.ckpt[(static_cast<size_t>(c) * 4 + i) * K + k] = x[i];
+                ++c;
+                to_ckpt = a.C;
             }
-            if ((t & 3) == 0) box_muller(noise_bits(nk, static_cast<uint32_t>(k), t / 4), z);
-            const float eps = sig * z[t & 3];
-            const float v = a.u_nom[t] + eps;
-            ak += a.G[t] * eps;
+            --to_ckpt;
+            const float eps = sig * z[s];
+            const float v = u4[s] + eps;
+            ak += g4[s] * eps;
             CartpoleDyn::step(x, &v, s_par, p.dt);
             dR += v * v;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const float d = x[i] - C[5 + i];
                 dQ[i] += d * d;
+            }
+        };
+        for (int t0 = 0; t0 < T; t0 += 4) {
+            float zn[4], un[4], gn[4];
+            group_normals<1>(nk, static_cast<uint32_t>(k), t0 + 4, QT, zn);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                un[s] = t0 + 4 + s < T ? a.u_nom[t0 + 4 + s] : 0.f;
+                gn[s] = t0 + 4 + s < T ? a.G[t0 + 4 + s] : 0.f;
+            }
+            if (t0 + 4 <= T) {
+#pragma unroll
+                for (int s = 0; s < 4; ++s) one_step(s);
+            } else {
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    if (t0 + s < T) one_step(s);
+            }
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                z[s] = zn[s];
+                u4[s] = un[s];
+                g4[s] = gn[s];
             }
         }
 #pragma unroll
