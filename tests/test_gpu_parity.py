@@ -150,6 +150,38 @@ def test_normals_two_million_against_the_oracle(m):
     assert np.all(err <= 8 * ulp + 2.0**-22)
 
 
+def test_cartpole_step_sin_cos_over_many_angles(m):
+    """One cart-pole step (the output-trajectory entry point, T = 1) from
+    pole angles across a wide range: uniform in (-pi, pi) and (-8192, 8192),
+    a few ulp from multiples of pi/2 (hard cases of an argument reduction),
+    and beyond.  The stepped velocities depend on sin(theta) and cos(theta)
+    through both accelerations; they must match the oracle's FP64 step from
+    the same FP32 state to the FP32 rounding of one step (a wrong quadrant
+    or term moves them by about dt * g / l)."""
+    rng = np.random.default_rng(29)
+    k = rng.integers(-5200, 5200, 300)
+    near = (k * (np.pi / 2)).astype(np.float32)
+    near = np.concatenate([near, np.nextafter(near, np.float32(np.inf)),
+                           np.nextafter(near, np.float32(-np.inf))])
+    angles = np.concatenate([rng.uniform(-np.pi, np.pi, 300), rng.uniform(-8192, 8192, 300),
+                             near, [8191.99, -8192.0, 8192.001, -9000.5, 20000.25, 0.0, -0.0]])
+    angles = angles.astype(np.float32).astype(np.float64)
+    p = as_f32_problem(W.cartpole(K=32, T=1))
+    ctl = m.MPPI.from_problem(p)
+    u = torch.tensor([1.25], dtype=torch.float32, device="cuda")
+    worst = 0.0
+    for th in angles:
+        x0 = np.array([0.3, -0.2, th, 0.7], np.float32).astype(np.float64)
+        traj = ctl.nominal_trajectory(torch.tensor(x0, dtype=torch.float32, device="cuda"), u)
+        g1 = traj[1].cpu().numpy().astype(np.float64)
+        o1 = oracle.dynamics_step(p, x0, np.array([1.25]))
+        err = np.abs(g1 - o1) / np.maximum(1.0, np.abs(o1))
+        worst = max(worst, float(err.max()))
+        assert np.all(err <= 4 * 2.0**-23), (th, g1, o1)
+    ctl.close()
+    print(f"max relative step difference {worst:.3g}")
+
+
 # --------------------------------------------------------------------------
 # the three single-instance workloads at full size
 # --------------------------------------------------------------------------
