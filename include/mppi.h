@@ -250,7 +250,10 @@ MPPI_API mppi_status mppi_set_params_device(mppi_ctx *ctx, const float *dyn_para
  * (same seed and step), for CARTPOLE + QUADRATIC + EULER only:
  * dL/dS_k = -(w_k / lambda)(a_k - sum_i w_i a_i), a_k = sum G eps_k, chained
  * through each rollout by a reverse (adjoint) sweep that recomputes states
- * from checkpoints stored every ceil(sqrt(T)) steps.
+ * from checkpoints stored every C steps, C = ceil(sqrt(T)) rounded up to a
+ * multiple of 4.  Every mppi_step of such a context stores those checkpoints
+ * (K * ceil(T / C) * 4 floats, allocated at create); the backward sweeps only
+ * the samples of non-zero weight.
  *   grad_u_new_d [T*nu] (device), grad_params_d [7] (device, overwritten).
  * Needs a prior mppi_step on this context; MPPI_ERR_UNSUPPORTED otherwise. */
 MPPI_API mppi_status mppi_step_backward(mppi_ctx *ctx, const float *grad_u_new_d,

@@ -82,314 +82,252 @@ __device__ __forceinline__ float weight_of(const StepParams &p, int k) {
 struct AdjParams {
     StepParams sp;
     const float *G;          // dL/du_new [T]
-    const float *x0, *u_nom; // inputs of the forward step (saved copies)
-    float *ckpt;             // [nck][4][K]
-    float *per_sample;       // [8][K]: a_k, dS/dQ0..3, dS/dR, dS/dl, dS/dm_c
-    int *kref;               // arg-min sample index
-    float *bpart;            // block partials
+    const float *u_nom;      // nominal controls of the forward step (saved copy)
+    const float *ckpt;       // [nck][4][K] states stored by the forward step's rollout
+    float *per_sample;       // [8][K]: a_k, dS/dQ0..3, dS/dR, dS/dl, dS/dm_c (non-zero weights only)
+    int *kref;               // arg-min sample index (reset to INT_MAX by the last block)
     float *grad_out;         // [7]
     int C, nck;
 };
 
-// Forward sweep: checkpoints, direct derivatives dS/dQ, dS/dR, a_k, and k*.
-__global__ void __launch_bounds__(kAdjThreads) adjoint_forward_kernel(const AdjParams a) {
+constexpr int kMaxSeg = 128;  // C <= 128 for T <= 16384
+
+// One kernel for the whole backward.
+//
+// Per sample of non-zero weight (from the forward step's list of them, or
+// every sample when the forward step scanned), one warp: the lanes take the
+// checkpoint segments of a window, each recomputing its segment's states
+// from the checkpoint the forward rollout stored, and leave per step t the
+// Jacobian entries at (x_t, v_t) and the running-cost gradient
+// 2 Q (x_t - goal) in shared memory, while accumulating the sample's direct
+// derivatives (a_k = sum G eps, dS/dQ, dS/dR); lane 0 then walks the window
+// backwards with multiply-adds only (the adjoint recurrence no longer waits
+// for sincos and divisions).  Windows of whole segments, last first.  The
+// lane sums are combined by a fixed warp tree.  The block that finishes
+// last (acquire-release ticket) forms the centred covariance over the
+// samples of non-zero weight and writes the gradient.
+constexpr int kAdjWarps = 4;     // warps per block
+constexpr int kRevWindow = 240;  // steps held in shared memory per warp
+constexpr int kRevStep = 12;     // floats per step: 8 Jacobian entries, 4 cost-gradient terms
+__global__ void __launch_bounds__(kAdjWarps * kWarp) adjoint_kernel(const AdjParams a) {
     const StepParams &p = a.sp;
     __shared__ float s_par[8];
+    __shared__ float s_step[kAdjWarps][kRevWindow * kRevStep];
+    __shared__ float s_xT[kAdjWarps][4];
+    __shared__ bool s_last;
     if (threadIdx.x < 4) s_par[threadIdx.x] = p.dyn_params[threadIdx.x];
     if (threadIdx.x == 0) s_par[4] = 1.0f / p.dyn_params[2];
     __syncthreads();
     const float *C = p.cost_params;  // Q(4), R(1), goal(4), s
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const NoiseKey nk = make_noise_key(p.seed, *p.last_step);
-    const int K = p.K, T = p.T, QT = (T + 3) / 4;
-    if (k < K) {
-        float x[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) x[i] = a.x0[i];
-        float dQ[4] = {0.f, 0.f, 0.f, 0.f}, dR = 0.f, ak = 0.f;
-        const float sig = p.sigma[0];
-        // four-step groups; the next group's normals, nominal controls and
-        // loss gradient are fetched while this group integrates, so Philox,
-        // Box-Muller and the loads stay off the state chain (the block drawn
-        // after the last group is never used)
-        float z[4], u4[4], g4[4];
-        group_normals<1>(nk, static_cast<uint32_t>(k), 0, QT, z);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            u4[s] = s < T ? a.u_nom[s] : 0.f;
-            g4[s] = s < T ? a.G[s] : 0.f;
-        }
-        int to_ckpt = 0, c = 0;  // steps to the next checkpoint (every a.C steps)
-        auto one_step = [&](int s) {
-            if (to_ckpt == 0) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) a.ckpt[(static_cast<size_t>(c) * 4 + i) * K + k] = x[i];
-                ++c;
-                to_ckpt = a.C;
-            }
-            --to_ckpt;
-            const float eps = sig * z[s];
-            const float v = u4[s] + eps;
-            ak += g4[s] * eps;
-            CartpoleDyn::step(x, &v, s_par, p.dt);
-            dR += v * v;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float d = x[i] - C[5 + i];
-                dQ[i] += d * d;
-            }
-        };
-        for (int t0 = 0; t0 < T; t0 += 4) {
-            float zn[4], un[4], gn[4];
-            group_normals<1>(nk, static_cast<uint32_t>(k), t0 + 4, QT, zn);
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                un[s] = t0 + 4 + s < T ? a.u_nom[t0 + 4 + s] : 0.f;
-                gn[s] = t0 + 4 + s < T ? a.G[t0 + 4 + s] : 0.f;
-            }
-            if (t0 + 4 <= T) {
-#pragma unroll
-                for (int s = 0; s < 4; ++s) one_step(s);
-            } else {
-#pragma unroll
-                for (int s = 0; s < 4; ++s)
-                    if (t0 + s < T) one_step(s);
-            }
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                z[s] = zn[s];
-                u4[s] = un[s];
-                g4[s] = gn[s];
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float d = x[i] - C[5 + i];
-            dQ[i] += C[9] * d * d;
-        }
-        a.per_sample[0 * K + k] = ak;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a.per_sample[(1 + i) * K + k] = dQ[i];
-        a.per_sample[5 * K + k] = dR;
-        // arg-min sample (smallest index among exact minima) as reference
-        if (p.scalars[4] != 0.f && p.S[k] == p.scalars[0]) atomicMin(a.kref, k);
-    }
-}
-
-constexpr int kMaxSeg = 128;  // C = ceil(sqrt T) <= 128 for T <= 16384
-
-// Reverse sweep: one warp per sample with non-zero weight (dS_k/dl, dS_k/dm_c).
-// The lanes recompute the checkpoint segments of a window in parallel, each
-// from its checkpoint, and leave per step t the Jacobian entries at
-// (x_t, v_t) and the running-cost gradient 2 Q (x_t - goal) in shared memory;
-// lane 0 then walks the window backwards with multiply-adds only (the
-// adjoint recurrence no longer waits for sincos and divisions).  Windows of
-// whole segments, last first; the arithmetic per step is the serial sweep's.
-constexpr int kRevWarps = 4;      // warps per block
-constexpr int kRevWindow = 240;   // steps held in shared memory per warp
-constexpr int kRevStep = 12;      // floats per step: 8 Jacobian entries, 4 cost-gradient terms
-__global__ void __launch_bounds__(kRevWarps * kWarp) adjoint_reverse_kernel(const AdjParams a) {
-    const StepParams &p = a.sp;
-    __shared__ float s_par[8];
-    __shared__ float s_step[kRevWarps][kRevWindow * kRevStep];
-    __shared__ float s_xT[kRevWarps][4];
-    if (threadIdx.x < 4) s_par[threadIdx.x] = p.dyn_params[threadIdx.x];
-    if (threadIdx.x == 0) s_par[4] = 1.0f / p.dyn_params[2];
-    __syncthreads();
-    const float *C = p.cost_params;
     const int K = p.K, T = p.T, CS = a.C, nck = a.nck;
     const int lane = threadIdx.x % kWarp, wib = threadIdx.x / kWarp;
-    const int warps = gridDim.x * kRevWarps, gw = blockIdx.x * kRevWarps + wib;
+    const int warps = gridDim.x * kAdjWarps, gw = blockIdx.x * kAdjWarps + wib;
     const NoiseKey nk = make_noise_key(p.seed, *p.last_step);
     const float Q[4] = {C[0], C[1], C[2], C[3]};
     const float gl[4] = {C[5], C[6], C[7], C[8]};
     const float s_term = C[9], sig = p.sigma[0], dt = p.dt;
     const int wseg = kRevWindow / CS;  // segments per window (>= 1: C <= kMaxSeg < kRevWindow)
+    const bool valid = p.scalars[4] != 0.f;
+    const int nnz = static_cast<int>(p.scalars[5]);  // listed non-zero weights, or -1: scan
+    const int n_items = !valid ? 0 : nnz >= 0 ? nnz : K;
     float *buf = s_step[wib];
-    for (int base = gw * kWarp; base < K; base += warps * kWarp) {
-        const int kl = base + lane;
-        unsigned todo = __ballot_sync(0xffffffffu, kl < K && weight_of(p, kl) != 0.f);
-        while (todo) {  // warp-uniform: one sample at a time
-            const int k = base + __ffs(todo) - 1;
-            todo &= todo - 1u;
-            float lam[4] = {0.f, 0.f, 0.f, 0.f};
-            float gl_p = 0.f, gmc = 0.f;
-            for (int c_end = nck; c_end > 0; c_end -= wseg) {
-                const int c_begin = max(0, c_end - wseg);
-                const int t0 = c_begin * CS, t1 = min(T, c_end * CS);
-                // recompute the window's segments, one per lane
-                for (int c = c_begin + lane; c < c_end; c += kWarp) {
-                    const int t_begin = c * CS, t_end = min(T, t_begin + CS);
-                    float x[4];
+
+    auto sweep = [&](int k) {  // warp-uniform: every lane calls it with the same k
+        float lam[4] = {0.f, 0.f, 0.f, 0.f};
+        float gl_p = 0.f, gmc = 0.f;
+        float ak = 0.f, dR = 0.f, dQ[4] = {0.f, 0.f, 0.f, 0.f};  // this lane's segments
+        for (int c_end = nck; c_end > 0; c_end -= wseg) {
+            const int c_begin = max(0, c_end - wseg);
+            const int t0 = c_begin * CS, t1 = min(T, c_end * CS);
+            for (int c = c_begin + lane; c < c_end; c += kWarp) {
+                const int t_begin = c * CS, t_end = min(T, t_begin + CS);
+                float x[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[i] = a.ckpt[(static_cast<size_t>(c) * 4 + i) * K + k];
+                float z[4];
+                for (int t = t_begin; t < t_end; ++t) {
+                    if (t == t_begin || (t & 3) == 0)
+                        box_muller(noise_bits(nk, static_cast<uint32_t>(k), t / 4), z);
+                    const float eps = sig * z[t & 3];
+                    const float v = a.u_nom[t] + eps;
+                    ak += a.G[t] * eps;
+                    dR += v * v;
+                    const CartpoleJac J = cartpole_jac(s_par, x[2], x[3], v);
+                    float *o = buf + (t - t0) * kRevStep;
+                    o[0] = J.xdd_th;
+                    o[1] = J.xdd_w;
+                    o[2] = J.thdd_th;
+                    o[3] = J.thdd_w;
+                    o[4] = J.xdd_l;
+                    o[5] = J.xdd_mc;
+                    o[6] = J.thdd_l;
+                    o[7] = J.thdd_mc;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) o[8 + i] = 2.0f * Q[i] * (x[i] - gl[i]);
+                    CartpoleDyn::step(x, &v, s_par, dt);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float d = x[i] - gl[i];
+                        dQ[i] += d * d;
+                    }
+                }
+                if (c == nck - 1) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        s_xT[wib][i] = x[i];
+                        const float d = x[i] - gl[i];
+                        dQ[i] += s_term * d * d;  // terminal cost
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                if (c_end == nck)  // adjoint at x_T: terminal cost and the last running cost
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
-                        x[i] = a.ckpt[(static_cast<size_t>(c) * 4 + i) * K + k];
-                    float z[4];
-                    for (int t = t_begin; t < t_end; ++t) {
-                        if (t == t_begin || (t & 3) == 0)
-                            box_muller(noise_bits(nk, static_cast<uint32_t>(k), t / 4), z);
-                        const float v = a.u_nom[t] + sig * z[t & 3];
-                        const CartpoleJac J = cartpole_jac(s_par, x[2], x[3], v);
-                        float *o = buf + (t - t0) * kRevStep;
-                        o[0] = J.xdd_th;
-                        o[1] = J.xdd_w;
-                        o[2] = J.thdd_th;
-                        o[3] = J.thdd_w;
-                        o[4] = J.xdd_l;
-                        o[5] = J.xdd_mc;
-                        o[6] = J.thdd_l;
-                        o[7] = J.thdd_mc;
+                        lam[i] = 2.0f * (1.0f + s_term) * Q[i] * (s_xT[wib][i] - gl[i]);
+                for (int t = t1 - 1; t >= t0; --t) {
+                    const float *o = buf + (t - t0) * kRevStep;
+                    // parameter gradient through x_{t+1} = x_t + dt f(x_t, v_t)
+                    gl_p += dt * (lam[1] * o[4] + lam[3] * o[6]);
+                    gmc += dt * (lam[1] * o[5] + lam[3] * o[7]);
+                    // lam_t = (I + dt df/dx)^T lam_{t+1}
+                    const float l0 = lam[0], l1 = lam[1], l2 = lam[2], l3 = lam[3];
+                    lam[1] = l1 + dt * l0;
+                    lam[2] = l2 + dt * (l1 * o[0] + l3 * o[2]);
+                    lam[3] = l3 + dt * (l2 + l1 * o[1] + l3 * o[3]);
+                    lam[0] = l0;
+                    if (t >= 1)  // running cost of step t-1 sits on x_t
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) o[8 + i] = 2.0f * Q[i] * (x[i] - gl[i]);
-                        CartpoleDyn::step(x, &v, s_par, dt);
-                    }
-                    if (c == nck - 1)
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) s_xT[wib][i] = x[i];
+                        for (int i = 0; i < 4; ++i) lam[i] += o[8 + i];
                 }
-                __syncwarp();
-                if (lane == 0) {
-                    if (c_end == nck)  // adjoint at x_T: terminal cost and the last running cost
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            lam[i] = 2.0f * (1.0f + s_term) * Q[i] * (s_xT[wib][i] - gl[i]);
-                    for (int t = t1 - 1; t >= t0; --t) {
-                        const float *o = buf + (t - t0) * kRevStep;
-                        // parameter gradient through x_{t+1} = x_t + dt f(x_t, v_t)
-                        gl_p += dt * (lam[1] * o[4] + lam[3] * o[6]);
-                        gmc += dt * (lam[1] * o[5] + lam[3] * o[7]);
-                        // lam_t = (I + dt df/dx)^T lam_{t+1}
-                        const float l0 = lam[0], l1 = lam[1], l2 = lam[2], l3 = lam[3];
-                        lam[1] = l1 + dt * l0;
-                        lam[2] = l2 + dt * (l1 * o[0] + l3 * o[2]);
-                        lam[3] = l3 + dt * (l2 + l1 * o[1] + l3 * o[3]);
-                        lam[0] = l0;
-                        if (t >= 1)  // running cost of step t-1 sits on x_t
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) lam[i] += o[8 + i];
-                    }
-                }
-                __syncwarp();
             }
-            if (lane == 0) {
-                a.per_sample[6 * K + k] = gl_p;
-                a.per_sample[7 * K + k] = gmc;
+            __syncwarp();
+        }
+        ak = warp_sum(ak);
+        dR = warp_sum(dR);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dQ[i] = warp_sum(dQ[i]);
+        if (lane == 0) {
+            a.per_sample[0 * K + k] = ak;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a.per_sample[(1 + i) * K + k] = dQ[i];
+            a.per_sample[5 * K + k] = dR;
+            a.per_sample[6 * K + k] = gl_p;
+            a.per_sample[7 * K + k] = gmc;
+            // arg-min sample (smallest index among exact minima) as reference
+            if (p.S[k] == p.scalars[0]) atomicMin(a.kref, k);
+        }
+    };
+    if (nnz >= 0) {  // the forward step's list of non-zero weights
+        for (int i = gw; i < n_items; i += warps) sweep(__ldcg(p.nz + i));
+    } else {
+        for (int base = gw * kWarp; base < n_items; base += warps * kWarp) {
+            const int kl = base + lane;
+            unsigned todo = __ballot_sync(0xffffffffu, kl < K && weight_of(p, kl) != 0.f);
+            while (todo) {
+                const int k = base + __ffs(todo) - 1;
+                todo &= todo - 1u;
+                sweep(k);
             }
         }
     }
-}
 
-// dL/dtheta = -(1/lambda) [sum w Da Dg - (sum w Da)(sum w Dg)] around k*,
-// block partials merged in a fixed order by the last block.  The fifteen sums
-// are reduced together: a warp-level tree each, then one shared-memory round.
-__global__ void __launch_bounds__(kAdjThreads) adjoint_reduce_kernel(const AdjParams a) {
-    const StepParams &p = a.sp;
-    constexpr int kNw = kAdjThreads / kWarp;
-    __shared__ float s_red[kNw][15][2];
+    // the barrier orders every warp's stores before thread 0's release
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_last = atomic_add_acq_rel(p.tickets + 3, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    // dL/dtheta = -(1/lambda) [sum w Da Dg - (sum w Da)(sum w Dg)] around k*
+    __shared__ float s_red[kAdjWarps][15][2];
     __shared__ float s_tot[15];
-    __shared__ bool s_last;
-    const int K = p.K;
-    const int kr = *a.kref;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x % kWarp, wid = threadIdx.x / kWarp;
-    float v[15];
+    const int kr = __ldcg(a.kref);
+    FloatPair v[15];
 #pragma unroll
-    for (int i = 0; i < 15; ++i) v[i] = 0.f;
-    if (k < K && kr < K) {
-        const float w = weight_of(p, k);
-        if (w != 0.f) {
-            const float da = a.per_sample[k] - a.per_sample[kr];
-            v[0] = w * da;
+    for (int i = 0; i < 15; ++i) v[i] = FloatPair{0.f, 0.f};
+    if (kr < K) {
+        float ref[8];
 #pragma unroll
-            for (int i = 0; i < 7; ++i) {
-                const float dg = a.per_sample[(1 + i) * K + k] - a.per_sample[(1 + i) * K + kr];
-                v[1 + i] = w * dg;
-                v[8 + i] = w * da * dg;
+        for (int i = 0; i < 8; ++i) ref[i] = __ldcg(a.per_sample + static_cast<size_t>(i) * K + kr);
+        for (int i = threadIdx.x; i < n_items; i += blockDim.x) {
+            const int k = nnz >= 0 ? __ldcg(p.nz + i) : i;
+            const float w = weight_of(p, k);
+            if (w == 0.f) continue;
+            const float da = __ldcg(a.per_sample + k) - ref[0];
+            v[0] = pair_add(v[0], FloatPair{w * da, 0.f});
+#pragma unroll
+            for (int j = 0; j < 7; ++j) {
+                const float dg = __ldcg(a.per_sample + static_cast<size_t>(1 + j) * K + k) - ref[1 + j];
+                v[1 + j] = pair_add(v[1 + j], FloatPair{w * dg, 0.f});
+                v[8 + j] = pair_add(v[8 + j], FloatPair{w * da * dg, 0.f});
             }
         }
     }
 #pragma unroll
     for (int i = 0; i < 15; ++i) {
-        const FloatPair t = warp_pair_sum(FloatPair{v[i], 0.f});
+        const FloatPair t = warp_pair_sum(v[i]);
         if (lane == 0) {
-            s_red[wid][i][0] = t.hi;
-            s_red[wid][i][1] = t.lo;
+            s_red[wib][i][0] = t.hi;
+            s_red[wib][i][1] = t.lo;
         }
     }
     __syncthreads();
     if (threadIdx.x < 15) {
         FloatPair acc{0.f, 0.f};
-        for (int w = 0; w < kNw; ++w)
+        for (int w = 0; w < kAdjWarps; ++w)
             acc = pair_add(acc, FloatPair{s_red[w][threadIdx.x][0], s_red[w][threadIdx.x][1]});
-        a.bpart[15 * blockIdx.x + threadIdx.x] = acc.hi + acc.lo;
-    }
-    // the barrier orders the partial stores before thread 0's fence and ticket
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(p.tickets + 3, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // value i on warp i % kNw: lanes take blocks lane, lane + 32, ... then a
-    // warp tree (fixed order)
-    for (int i = wid; i < 15; i += kNw) {
-        FloatPair acc{0.f, 0.f};
-        for (int b = lane; b < static_cast<int>(gridDim.x); b += kWarp)
-            acc = pair_add(acc, FloatPair{__ldcg(a.bpart + 15 * b + i), 0.f});
-        acc = warp_pair_sum(acc);
-        if (lane == 0) s_tot[i] = acc.hi + acc.lo;
+        s_tot[threadIdx.x] = acc.hi + acc.lo;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int i = 0; i < 7; ++i)
             a.grad_out[i] = (kr < K) ? -(s_tot[8 + i] - s_tot[0] * s_tot[1 + i]) / p.lambda : 0.f;
+        *a.kref = 0x7fffffff;  // ready for the next backward
         p.tickets[3] = 0u;
     }
 }
 
 }  // namespace
 
-size_t adjoint_scratch_floats(int K, int T) {
+// ceil(sqrt(T)) rounded up to a multiple of 4, so that the forward rollouts
+// store the checkpoints at the start of their four-step groups
+int adjoint_checkpoint_every(int T) {
     int C = 1;
     while (C * C < T) ++C;
-    const int nck = (T + C - 1) / C;
-    const int blocks = (K + kAdjThreads - 1) / kAdjThreads;
-    return static_cast<size_t>(nck) * 4 * K + 8 * static_cast<size_t>(K) + 15 * blocks + 4;
+    return 4 * ((C + 3) / 4);
 }
 
+size_t adjoint_checkpoint_floats(int K, int T, int nx) {
+    const int C = adjoint_checkpoint_every(T);
+    return static_cast<size_t>((T + C - 1) / C) * nx * K;
+}
+
+// per-sample values [8][K] and the reference index
+size_t adjoint_scratch_floats(int K, int) { return 8 * static_cast<size_t>(K) + 4; }
+
 cudaError_t launch_adjoint(const mppi_ctx &c, const StepParams &sp, const float *G,
-                           const float *x0, const float *u_nom, float *scratch,
-                           float *grad_out, cudaStream_t s) {
+                           const float *u_nom, float *scratch, bool fresh, float *grad_out,
+                           cudaStream_t s) {
     AdjParams a;
     a.sp = sp;
     a.G = G;
-    a.x0 = x0;
     a.u_nom = u_nom;
-    int C = 1;
-    while (C * C < c.T) ++C;
-    if (C > kMaxSeg) return cudaErrorInvalidValue;
-    a.C = C;
-    a.nck = (c.T + C - 1) / C;
-    a.ckpt = scratch;
-    a.per_sample = a.ckpt + static_cast<size_t>(a.nck) * 4 * c.K;
-    const int blocks = (c.K + kAdjThreads - 1) / kAdjThreads;
-    a.bpart = a.per_sample + 8 * static_cast<size_t>(c.K);
-    a.kref = reinterpret_cast<int *>(a.bpart + 15 * blocks);
+    a.C = c.scr.ckpt_every;
+    if (a.C > kMaxSeg) return cudaErrorInvalidValue;
+    a.nck = (c.T + a.C - 1) / a.C;
+    a.ckpt = c.scr.ckpt;
+    a.per_sample = scratch;
+    a.kref = reinterpret_cast<int *>(scratch + 8 * static_cast<size_t>(c.K));
     a.grad_out = grad_out;
-    cudaError_t e = cudaMemsetAsync(a.kref, 0x7f, sizeof(int), s);  // "no reference yet"
-    if (e != cudaSuccess) return e;
-    adjoint_forward_kernel<<<blocks, kAdjThreads, 0, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // reverse sweep: enough warps to cover K in 32-sample strides, at most
-    // two blocks per SM
-    const int rev_blocks = std::max(1, std::min((c.K + kRevWarps * kWarp - 1) / (kRevWarps * kWarp),
-                                                2 * c.num_sms));
-    adjoint_reverse_kernel<<<rev_blocks, kRevWarps * kWarp, 0, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    adjoint_reduce_kernel<<<blocks, kAdjThreads, 0, s>>>(a);
+    if (fresh) {  // a new scratch: the reference index starts at "none yet"
+        const cudaError_t e = cudaMemsetAsync(a.kref, 0x7f, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+    }
+    // enough warps for the listed samples, at most two blocks per SM
+    const int blocks = std::max(1, std::min((c.K + kAdjWarps - 1) / kAdjWarps, 2 * c.num_sms));
+    adjoint_kernel<<<blocks, kAdjWarps * kWarp, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -92,7 +92,7 @@ void free_ctx(mppi_ctx *c) {
     void *ptrs[] = {c->d_dyn, c->d_cost, c->d_map, c->scr.S, c->scr.w, c->scr.nz, c->scr.cand,
                     c->scr.partials, c->scr.upartials,
                     c->scr.scalars, c->scr.tickets, c->scr.status, c->scr.counter,
-                    c->scr.last_step, c->scr.ckpt, c->scr.grad_partials, c->scr.io,
+                    c->scr.last_step, c->scr.ckpt, c->scr.io,
                     c->scr.saved_in, c->scr.adj};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -216,6 +216,8 @@ StepParams make_params(const mppi_ctx &c) {
     p.counter = c.scr.counter;
     p.last_step = c.scr.last_step;
     p.saved_in = c.differentiable ? c.scr.saved_in : nullptr;
+    p.ckpt = c.differentiable ? c.scr.ckpt : nullptr;
+    p.ckpt_every = c.scr.ckpt_every;
     p.checked = c.checked;
     return p;
 }
@@ -370,6 +372,7 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
     plan_launch(*c);
     c->differentiable = dyn->kind == MPPI_DYN_CARTPOLE && cost->kind == MPPI_COST_QUADRATIC &&
                         dyn->integrator == MPPI_EULER;
+    if (c->differentiable) c->scr.ckpt_every = mppi::adjoint_checkpoint_every(T);
 
     const int Q = nu * ((T + 3) / 4);
     const size_t max_blocks = (4 * static_cast<size_t>(K) + 31) / 32;  // 32-thread blocks, 4 lanes
@@ -390,6 +393,8 @@ mppi_status mppi_create(const mppi_dynamics_desc *dyn, const mppi_cost_desc *cos
         (c->differentiable &&
          (e = dalloc(&c->scr.saved_in, static_cast<size_t>(nx) + static_cast<size_t>(T) * nu)) !=
              cudaSuccess) ||
+        (c->differentiable &&
+         (e = dalloc(&c->scr.ckpt, mppi::adjoint_checkpoint_floats(K, T, nx))) != cudaSuccess) ||
         (e = dalloc(&c->d_dyn, c->dyn_params_h.size())) != cudaSuccess ||
         (e = dalloc(&c->d_cost, c->cost_params_h.size())) != cudaSuccess) {
         free_ctx(c);
@@ -605,7 +610,8 @@ mppi_status mppi_step_backward(mppi_ctx *ctx, const float *grad_u_new_d, float *
         return fail(ctx, MPPI_ERR_INVALID_ARG, "grad_u_new and grad_params must be device pointers");
     cudaError_t e;
     const size_t need = mppi::adjoint_scratch_floats(ctx->K, ctx->T);
-    if (ctx->scr.adj_floats < need) {
+    const bool fresh = ctx->scr.adj_floats < need;
+    if (fresh) {
         if (ctx->scr.adj) cudaFree(ctx->scr.adj);
         ctx->scr.adj = nullptr;
         ctx->scr.adj_floats = 0;
@@ -616,9 +622,8 @@ mppi_status mppi_step_backward(mppi_ctx *ctx, const float *grad_u_new_d, float *
     StepParams p = make_params(*ctx);
     {
         ProfScope ps(ctx, MPPI_PROF_ADJOINT);
-        e = mppi::launch_adjoint(*ctx, p, grad_u_new_d, ctx->scr.saved_in,
-                                 ctx->scr.saved_in + ctx->nx, ctx->scr.adj, grad_params_d,
-                                 ctx->stream);
+        e = mppi::launch_adjoint(*ctx, p, grad_u_new_d, ctx->scr.saved_in + ctx->nx,
+                                 ctx->scr.adj, fresh, grad_params_d, ctx->stream);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
     return MPPI_OK;

@@ -35,10 +35,8 @@ struct Scratch {
     unsigned int *status = nullptr;     // [1] device status word
     unsigned long long *counter = nullptr;    // [1] step counter
     unsigned long long *last_step = nullptr;  // [1] step used by the latest mppi_step
-    float *ckpt = nullptr;              // adjoint checkpoints (lazily allocated)
-    size_t ckpt_floats = 0;
-    float *grad_partials = nullptr;     // adjoint block partials
-    size_t grad_partials_floats = 0;
+    float *ckpt = nullptr;              // [nck][nx][K] states every ckpt_every steps (differentiable contexts)
+    int ckpt_every = 0;
     float *io = nullptr;                // staging for mppi_step_host: x0, u_nom, u_new, stats
     float *saved_in = nullptr;          // x0 and u_nom of the latest step (differentiable contexts)
     float *adj = nullptr;               // adjoint scratch (allocated by the first backward)
@@ -62,6 +60,8 @@ struct StepParams {
     float *w;
     int *nz, *cand;
     float *saved_in;                    // non-null: block 0 of the rollout copies x0, u_nom here
+    float *ckpt;                        // non-null: the rollout stores x_t of every sample here,
+    int ckpt_every;                     //   [t / ckpt_every][nx][K], at t = 0, ckpt_every, ...
     unsigned int *tickets, *status;
     unsigned long long *counter, *last_step;
     int checked;                        // check computed indices (mppi_options.checked)
@@ -150,10 +150,12 @@ cudaError_t launch_store_u64(unsigned long long *dst, unsigned long long v, cuda
 cudaLaunchConfig_t pdl_config(dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               cudaLaunchAttribute *attr);
 // adjoint.cu: backward of the cart-pole step
+int adjoint_checkpoint_every(int T);                      // ceil(sqrt(T)), multiple of 4
+size_t adjoint_checkpoint_floats(int K, int T, int nx);  // stored by every forward step
 size_t adjoint_scratch_floats(int K, int T);
 cudaError_t launch_adjoint(const mppi_ctx &c, const StepParams &sp, const float *G,
-                           const float *x0, const float *u_nom, float *scratch,
-                           float *grad_out, cudaStream_t s);
+                           const float *u_nom, float *scratch, bool fresh, float *grad_out,
+                           cudaStream_t s);
 // rollout_quad.cu: four lanes per quadrotor sample
 bool quad_group_applicable(const mppi_ctx &c);
 size_t quad_group_smem_bytes(const mppi_ctx &c);

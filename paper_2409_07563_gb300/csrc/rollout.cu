@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(256) rollout_kernel(const StepParams p) {
         for (int i = tid; i < p.T * NU; i += nt) p.saved_in[NX + i] = s_u[i];
     }
     const SampleArgs args{p.T, p.dt, p.lam_beta, p.sigma, p.ivar, p.x0, s_u, s_dyn, s_cost,
-                          CostCtx{p.map, p.map_h, p.map_w, p.checked ? p.status : nullptr}, make_noise_key(p.seed, *p.counter)};
+                          CostCtx{p.map, p.map_h, p.map_w, p.checked ? p.status : nullptr},
+                          make_noise_key(p.seed, *p.counter), p.ckpt, p.ckpt_every, p.K};
     const int k = blockIdx.x * nt + tid;
     float S = __int_as_float(0x7f800000);  // inactive lanes take no part
     if (k < p.K) {
@@ -131,11 +132,25 @@ __global__ void __launch_bounds__(256) pair_rollout_kernel(const StepParams p) {
         float x[NX];
 #pragma unroll
         for (int i = 0; i < NX; ++i) x[i] = p.x0[i];
+        // checkpoints for a later backward: x_t at t = 0, ckpt_every, ... (a
+        // multiple of the half, so they fall on half boundaries)
+        float *const ckpt = k < p.K ? p.ckpt : nullptr;
+        int to_ck = 0, ck = 0;
         pair_sync(bar_id);  // the controls of half 0 are in the ring
         for (int hh = 0; hh < nh; ++hh) {
             const float *vb = ring_v + (hh % 3) * kVSlot;
             float *xb = ring_x + (hh & 1) * kXSlot;
             const int ns = min(H, T - hh * H);
+            if (ckpt) {
+                if (to_ck == 0) {
+#pragma unroll
+                    for (int i = 0; i < NX; ++i)
+                        ckpt[(static_cast<size_t>(ck) * NX + i) * p.K + k] = x[i];
+                    ++ck;
+                    to_ck = p.ckpt_every;
+                }
+                to_ck -= H;
+            }
             auto one = [&](int s) {
                 float v[NU];
 #pragma unroll

@@ -35,18 +35,6 @@ constexpr int kListPerThread = 8;
 // Candidate slots of its block that each merging thread loads with the
 // block's partials.
 constexpr int kSpecCand = 4;
-// Device-scope atomic add with acquire and release semantics: the writes
-// this thread has made or observed (a barrier before it) become visible to
-// whoever reads the result later, and this thread sees theirs.
-__device__ __forceinline__ unsigned int atomic_add_acq_rel(unsigned int *a, unsigned int v) {
-    unsigned int old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
-                 : "=r"(old)
-                 : "l"(a), "r"(v)
-                 : "memory");
-    return old;
-}
-
 // Order-preserving unsigned key of a float (for atomicMin on costs).
 __device__ __forceinline__ unsigned int float_key(float f) {
     const unsigned int b = __float_as_uint(f);

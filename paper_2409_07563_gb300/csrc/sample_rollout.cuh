@@ -18,6 +18,11 @@ struct SampleArgs {
     const float *s_dyn, *s_cost;
     CostCtx cc;
     NoiseKey nk;
+    // non-null: x_t of sample k is stored at [t / ckpt_every][nx][ckpt_K] for
+    // t = 0, ckpt_every, ... (checkpoints for a later backward; ckpt_every is
+    // a multiple of 4)
+    float *ckpt = nullptr;
+    int ckpt_every = 0, ckpt_K = 0;
 };
 
 template <class Dyn, class Cost>
@@ -39,6 +44,7 @@ __device__ __forceinline__ float generic_sample_cost(const SampleArgs &a, uint32
     // the block drawn after the last group is never used
     float z[4 * NU];
     group_normals<NU>(a.nk, k, 0, QT, z);
+    int to_ck = 0, ck = 0;  // steps to the next checkpoint, its index
     auto one_step = [&](int t, int s) {
         float v[NU];
         float is = 0.f;
@@ -52,6 +58,16 @@ __device__ __forceinline__ float generic_sample_cost(const SampleArgs &a, uint32
         J.add(Cost::running(x, v, a.s_cost, a.cc) + a.lam_beta * is);
     };
     for (int t0 = 0; t0 < T; t0 += 4) {
+        if (a.ckpt) {  // (ckpt_every is a multiple of the four-step group)
+            if (to_ck == 0) {
+#pragma unroll
+                for (int i = 0; i < NX; ++i)
+                    a.ckpt[(static_cast<size_t>(ck) * NX + i) * a.ckpt_K + k] = x[i];
+                ++ck;
+                to_ck = a.ckpt_every;
+            }
+            to_ck -= 4;
+        }
         float zn[4 * NU];
         if (Dyn::kPipelineNoise) group_normals<NU>(a.nk, k, t0 + 4, QT, zn);
         if (t0 + 4 <= T) {
