@@ -38,7 +38,7 @@ struct CartpoleDyn {
         sincosf(x[2], &s, &c);
         const float thd = x[3], f = v[0];
         const float D = m_c + m_p * s * s;
-        const float rD = __frcp_rn(D);  // correctly rounded 1/D, shared by both
+        const float rD = rcp_newton(D);  // 1/D within an ulp (D > 0 for physical masses), shared by both
         const float xdd = (f + m_p * s * (l * thd * thd + g * c)) * rD;
         const float thdd = (-f * c - m_p * l * thd * thd * c * s - (m_c + m_p) * g * s) * rD * P[4];
         x[0] += dt * x[1];
