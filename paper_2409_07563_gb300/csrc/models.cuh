@@ -35,7 +35,7 @@ struct CartpoleDyn {
                                                 float dt) {
         const float m_c = P[0], m_p = P[1], l = P[2], g = P[3];
         float s, c;
-        sincosf(x[2], &s, &c);
+        sincos_cw(x[2], &s, &c);
         const float thd = x[3], f = v[0];
         const float D = m_c + m_p * s * s;
         const float rD = rcp_newton(D);  // 1/D within an ulp (D > 0 for physical masses), shared by both
