@@ -45,7 +45,7 @@ struct CartpoleJac {
 __device__ __forceinline__ CartpoleJac cartpole_jac(const float *P, float th, float w, float f) {
     const float m_c = P[0], m_p = P[1], l = P[2], g = P[3];
     float s, c;
-    sincosf(th, &s, &c);
+    sincos_cw(th, &s, &c);
     const float w2 = w * w;
     const float D = m_c + m_p * s * s;
     const float iD = 1.0f / D, il = 1.0f / l;

@@ -7,7 +7,7 @@
 // v_t = u_t + sigma z_t into the ring with the importance term, integrates
 // the pose (x, y, yaw) of the kinematic bicycle from the dynamics warp's
 // (v, delta) before each step and the yaw-rate residual (FP32, accurate
-// sincosf / tanf, Euler) -- the pose feeds nothing back into the MLP -- and
+// sincos_cw / tanf, Euler) -- the pose feeds nothing back into the MLP -- and
 // scores x_{t+1} with the bilinear costmap and the speed term.  It exchanges
 // with its dynamics warp through a double-buffered ring of kMlpH steps per
 // half and one named barrier (bar_threads: the cost warp and its dynamics
@@ -83,7 +83,7 @@ __device__ __forceinline__ float bicycle_cost_warp(const StepParams &p, const fl
 #pragma unroll
         for (int s = 0; s < kMlpH; ++s) {
             float sn, cs;
-            sincosf(yaw, &sn, &cs);
+            sincos_cw(yaw, &sn, &cs);
             const float xd0 = q[s].x * cs, xd1 = q[s].x * sn;
             const float xd2 = q[s].x * tn[s] * inv_L + q[s].z;
             px += p.dt * xd0;

@@ -167,7 +167,7 @@ struct BicycleMlpDyn {
         float r[4];
         residual(in, P, r);
         float s, c;
-        sincosf(x[2], &s, &c);
+        sincos_cw(x[2], &s, &c);
         const float xd0 = x[3] * c, xd1 = x[3] * s;
         const float xd2 = x[3] * tanf(x[4]) / P[kL] + r[0];
         const float xd3 = v[0] + r[1];

@@ -22,7 +22,8 @@
 // lanes).  Weight rows are stored with 16 bytes of padding per 16 units, so
 // the four unit quarters fall on different bank groups.  The noise, the kinematic bicycle and
 // the cost are computed by all four lanes of the sample on identical values;
-// lane 0 reports S.  FP32 throughout (accurate tanhf, sincosf, tanf).
+// lane 0 reports S.  FP32 throughout (accurate tanhf and tanf, sin/cos within
+// an ulp by sincos_cw).
 #include "device_common.cuh"
 #include "models.cuh"
 #include "mppi_internal.h"
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(256) bicycle_mlp_f32_kernel(const StepParams p
                         r2 = s_b3[2] + part[j][2], r3 = s_b3[3] + part[j][3];
             // kinematic bicycle + residual, Euler (as BicycleMlpDyn::step)
             float sn, cs;
-            sincosf(x[j][2], &sn, &cs);
+            sincos_cw(x[j][2], &sn, &cs);
             const float xd0 = x[j][3] * cs, xd1 = x[j][3] * sn;
             const float xd2 = x[j][3] * tanf(x[j][4]) * inv_L + r0;
             const float xd3 = va[j] + r1;
