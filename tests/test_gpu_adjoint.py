@@ -26,8 +26,8 @@ def m():
     return mod
 
 
-def gpu_grad(m, p):
-    ctl = m.MPPI.from_problem(p)
+def gpu_grad(m, p, **kw):
+    ctl = m.MPPI.from_problem(p, **kw)
     x0 = torch.tensor(p["x0"], dtype=torch.float32, device="cuda")
     u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device="cuda")
     target = torch.tensor(p["u_target"].reshape(-1), dtype=torch.float32, device="cuda")
@@ -68,6 +68,46 @@ def test_adjoint_ragged(m, K, T):
     g_gpu, _ = gpu_grad(m, p)
     g_ref = oracle_grad(p)
     assert rel_err(g_gpu, g_ref) <= 1e-3, (g_gpu, g_ref)
+
+
+@pytest.mark.parametrize("opts", [dict(rollout_variant=1, block_threads=32),
+                                  dict(rollout_variant=1, block_threads=128),
+                                  dict(block_threads=96), dict(block_threads=192)])
+@pytest.mark.parametrize("K,T", [(1000, 37), (2048, 100)])
+def test_adjoint_after_every_forward_kernel(m, opts, K, T):
+    """The checkpoints the backward recomputes from are stored by the forward
+    step's rollout: by the warp triples (one or two per block) and by the
+    one-sample-per-thread kernel, at the start of their four-step groups."""
+    base = W.differentiable(K=K, T=T)
+    base["lam"] = 20.0
+    p = as_f32_problem(base)
+    g_gpu, _ = gpu_grad(m, p, **opts)
+    g_ref = oracle_grad(p)
+    assert rel_err(g_gpu, g_ref) <= 1e-3, (opts, g_gpu, g_ref)
+
+
+def test_adjoint_uses_the_latest_step(m):
+    """A second forward step overwrites the checkpoints and the saved inputs;
+    the backward differentiates that step (counter 1, new nominal controls)."""
+    base = W.differentiable(K=1024, T=60)
+    base["lam"] = 15.0
+    p = as_f32_problem(base)
+    ctl = m.MPPI.from_problem(p)
+    x0 = torch.tensor(p["x0"], dtype=torch.float32, device="cuda")
+    u0 = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device="cuda")
+    ctl.step(x0, u0)
+    u1 = np.float32(0.3) * np.ones_like(p["u_nom"])
+    out = ctl.step(x0, torch.tensor(u1.reshape(-1), dtype=torch.float32, device="cuda"))
+    target = torch.tensor(p["u_target"].reshape(-1), dtype=torch.float32, device="cuda")
+    g = ctl.backward(2.0 * (out["u_new"].reshape(-1) - target))
+    torch.cuda.synchronize()
+    q = dict(p)
+    q["u_nom"] = u1.astype(np.float64)
+    r = oracle.mppi_step(q, step=1, n_threads=n_threads())
+    g_ref, st = oracle.mppi_grad_cartpole(q, 2.0 * (r["u_new"] - q["u_target"]), step=1,
+                                          n_threads=n_threads())
+    assert st == 0
+    assert rel_err(g.cpu().numpy().astype(np.float64), g_ref) <= 1e-3
 
 
 def test_adjoint_matches_central_differences(m):
