@@ -29,12 +29,6 @@ constexpr int kPairConstFloats = static_cast<int>(sizeof(QuadPairConst) / sizeof
 constexpr int kPairListedMax = 6;
 constexpr int kLowRegPairListedMax = 4;
 
-// Warp role by warp slot (slot = warp / groups per block), one nibble each:
-// dynamics (0), noise channels 0-1 (1), noise channels 2-3 (2), cost (3).
-// (Measured on GB300 at K = 8192: pairing each dynamics warp with a cost warp
-// on one sub-partition, and the noise warps with each other, was slower.)
-constexpr unsigned kPairRoleOrder = 0x3210u;
-
 constexpr int kPairH = 4;  // steps per ring half (whole Philox blocks of four steps)
 static_assert(kPairH % 4 == 0, "a ring half holds whole noise blocks");
 constexpr int kRingXPair = 2 * kPairH * 4 * kWarp;  // float4: [half][step][group][lane]

@@ -40,14 +40,14 @@ namespace mppi {
 
 namespace {
 
-// Block = G groups of 32 samples on 4G warps; group j synchronises on named
-// barrier 1 + j.  A block's warp w runs on SM sub-partition w mod 4, so with
-// two groups the warps are ordered (dynamics, noise 0-1, cost, noise 2-3) x
-// (group 0, group 1): each sub-partition holds a dynamics and a cost warp, or
-// two noise warps, which balances their instruction counts.  One group: warps
-// 0-3 in role order.  kLowReg: the build for large K, held to 128 registers
-// so that two blocks share an SM.  The spheres are staged in shared memory
-// (one by one, and in pairs).
+// Block = G groups of 32 samples: warps [0, G) integrate, [G, 3G) draw
+// the noise (channels 0-1, then 2-3), [3G, 4G) score; group j synchronises
+// on named barrier 1 + j.  (A block's warp w runs on SM sub-partition
+// w mod 4, so with two groups each sub-partition holds a dynamics and a
+// noise warp, or a noise and a cost warp; pairing each dynamics warp with a
+// cost warp instead measured slower.)  kLowReg: the build for large K, held
+// to 128 registers so that two blocks share an SM.  The spheres are staged
+// in shared memory (one by one, and in pairs).
 template <bool kObstacles, bool kLowReg>
 __global__ void __launch_bounds__(256, kLowReg ? 2 : 1)
     quad_pair_kernel(const StepParams p, const QuadPairConst c) {
@@ -56,9 +56,7 @@ __global__ void __launch_bounds__(256, kLowReg ? 2 : 1)
     const int tid = threadIdx.x, nt = blockDim.x;
     const int ngroups = nt / (4 * kWarp);
     const int warp = tid / kWarp, lane = tid % kWarp;
-    // role of warp slot warp / G, one nibble each: 0, 1, 3, 2
-    const int role = static_cast<int>((kPairRoleOrder >> (4 * (warp / ngroups))) & 0xfu);
-    const int group = warp % ngroups;
+    const int role = warp / ngroups, group = warp % ngroups;
     float *s_u = smem + ngroups * kPairGroupFloats;
     float *s_dyn = s_u + round_up4(4 * T);
     float *s_red = s_dyn + 8;
@@ -186,7 +184,7 @@ cudaError_t launch_quad_pair(const mppi_ctx &c, const StepParams &p) {
     for (int j = 0; j < kPairSpheres / 2; ++j) {
         float q[2][4];
         for (int h = 0; h < 2; ++h) {
-            const int i = 2 * j + h < n && ordered ? c.sphere_order[2 * j + h] : 2 * j + h;
+            const int i = (2 * j + h < n && ordered) ? c.sphere_order[2 * j + h] : 2 * j + h;
             if (2 * j + h < n) {
                 const float r = cp[33 + 4 * i + 3];
                 q[h][0] = cp[33 + 4 * i];

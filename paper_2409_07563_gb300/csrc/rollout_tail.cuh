@@ -117,11 +117,14 @@ __device__ inline void finish_weights(const StepParams &p, bool list_mode, int n
 // /eta, in sample order, built from the blocks' candidates (k, S_k), and --
 // when that list is short -- the update u_new = u_nom + sum_k w_k eps_k itself.
 //
-// While the grid has no more blocks than this block has threads, every
-// global read of the merge is one parallel round trip: each thread loads one
-// block's partials, then at most kListPerThread candidate pairs, located by a
-// search in the blocks' candidate offsets; the non-zero weights are compacted
-// in registers.  Larger grids walk contiguous block ranges per thread.
+// While the grid has no more blocks than this block has threads, each
+// thread loads one block's partials together with that block's first
+// kSpecCand candidate slots (one round trip).  When no block has more
+// candidates than that, the non-zero weights are compacted from those
+// registers with one scan; otherwise a second round trip loads at most
+// kListPerThread candidate pairs per thread, located by a search in the
+// blocks' candidate offsets.  Larger grids walk contiguous block ranges per
+// thread.
 constexpr int kMaxFinalizeThreads = 512;
 __device__ inline void finalize_weights(const StepParams &p, int nblocks, int cand_stride,
                                         float *red, const float *s_unom) {
