@@ -94,10 +94,11 @@ class MPPI:
 
     def _use_stream(self, L, stream):
         """mppi_set_stream, skipped when the context already uses that stream."""
-        hs = _stream_handle(stream)
-        if hs.value != self._stream_val:
-            check(L.mppi_set_stream(self._h, hs), "mppi_set_stream", self._h)
-            self._stream_val = hs.value
+        import torch
+        s = (torch.cuda.current_stream() if stream is None else stream).cuda_stream
+        if s != self._stream_val:
+            check(L.mppi_set_stream(self._h, ctypes.c_void_p(s)), "mppi_set_stream", self._h)
+            self._stream_val = s
 
     @classmethod
     def from_problem(cls, p: dict, **kw):
@@ -178,10 +179,7 @@ class MPPI:
         """``mppi_step_host`` on raw host addresses (e.g. pinned torch tensors)."""
         L = load()
         self._use_stream(L, stream)
-        fp = ctypes.POINTER(ctypes.c_float)
-        st = L.mppi_step_host(self._h, ctypes.cast(x0_ptr, fp), ctypes.cast(u_nom_ptr, fp),
-                              ctypes.cast(u_new_ptr, fp),
-                              ctypes.cast(stats_ptr, fp) if stats_ptr else None)
+        st = L.mppi_step_host_addr(self._h, x0_ptr, u_nom_ptr, u_new_ptr, stats_ptr or None)
         check(st, "mppi_step_host", self._h)
 
     def set_params(self, dyn_params=None, cost_params=None):

@@ -100,6 +100,10 @@ def load() -> ctypes.CDLL:
                  "mppi_profile_read", "mppi_set_iterations", "mppi_nominal_trajectory",
                  "mppi_shift", "mppi_set_cem"):
         getattr(L, name).restype = ctypes.c_int
+    # mppi_step_host on raw host addresses (Python ints): the same symbol with
+    # void-pointer arguments, so a per-step call needs no pointer casts
+    L.mppi_step_host_addr = ctypes.CFUNCTYPE(ctypes.c_int, vp, vp, vp, vp, vp)(
+        ("mppi_step_host", L))
     _optional(L)
     _lib = L
     return L

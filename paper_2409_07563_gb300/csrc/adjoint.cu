@@ -31,8 +31,6 @@
 namespace mppi {
 namespace {
 
-constexpr int kAdjThreads = 128;
-
 struct CartpoleJac {
     // df/dx entries that are not 0/1 and df/d(l, m_c) of xdd (row 1) and thdd (row 3)
     float xdd_th, xdd_w, thdd_th, thdd_w;
@@ -220,7 +218,14 @@ __global__ void __launch_bounds__(kAdjWarps * kWarp) adjoint_kernel(const AdjPar
         }
     };
     if (nnz >= 0) {  // the forward step's list of non-zero weights
-        for (int i = gw; i < n_items; i += warps) sweep(__ldcg(p.nz + i));
+        for (int i = gw; i < n_items; i += warps) {
+            const int k = __ldcg(p.nz + i);
+            if (p.checked && !(k >= 0 && k < K)) {  // (uniform: one k per warp)
+                if (lane == 0) flag_check(p.status);
+                continue;
+            }
+            sweep(k);
+        }
     } else {
         for (int base = gw * kWarp; base < n_items; base += warps * kWarp) {
             const int kl = base + lane;
@@ -252,6 +257,10 @@ __global__ void __launch_bounds__(kAdjWarps * kWarp) adjoint_kernel(const AdjPar
         for (int i = 0; i < 8; ++i) ref[i] = __ldcg(a.per_sample + static_cast<size_t>(i) * K + kr);
         for (int i = threadIdx.x; i < n_items; i += blockDim.x) {
             const int k = nnz >= 0 ? __ldcg(p.nz + i) : i;
+            if (p.checked && !(k >= 0 && k < K)) {
+                flag_check(p.status);
+                continue;
+            }
             const float w = weight_of(p, k);
             if (w == 0.f) continue;
             const float da = __ldcg(a.per_sample + k) - ref[0];

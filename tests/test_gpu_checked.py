@@ -75,3 +75,26 @@ def test_checked_mode_on_a_two_by_two_map(m):
 def test_checked_option_rejects_other_values(m):
     with pytest.raises(m.MPPIError):
         m.MPPI.from_problem(W.cartpole(K=16, T=4), checked=2)
+
+
+@pytest.mark.parametrize("lam", [1.0, 200.0])
+def test_checked_backward_is_clean_and_identical(m, lam):
+    """The backward reads sample indices from the forward step's list of
+    non-zero weights (lambda = 1) or scans every sample (lambda = 200): in
+    checked mode the gradient must equal the unchecked one bit for bit and
+    the status word stay clean."""
+    base = W.differentiable(K=2048, T=50)
+    base["lam"] = lam
+    p = as_f32_problem(base)
+    grads = []
+    for checked in (1, 0):
+        ctl = m.MPPI.from_problem(p, checked=checked)
+        x0 = torch.tensor(p["x0"], dtype=torch.float32, device="cuda")
+        u = torch.tensor(p["u_nom"].reshape(-1), dtype=torch.float32, device="cuda")
+        out = ctl.step(x0, u)
+        target = torch.tensor(p["u_target"].reshape(-1), dtype=torch.float32, device="cuda")
+        g = ctl.backward(2.0 * (out["u_new"].reshape(-1) - target))
+        torch.cuda.synchronize()
+        grads.append(g.cpu().numpy())
+        assert ctl.poll_status() == 0
+    assert np.array_equal(grads[0], grads[1])
