@@ -23,9 +23,9 @@ struct QuadPairConst {
 };
 constexpr int kPairConstFloats = static_cast<int>(sizeof(QuadPairConst) / sizeof(float));
 // Up to this many sphere pairs near a warp's positions, the cost warp tests
-// only those (held in registers over a ring half); above, every pair.  The
-// single-instance build held to 128 registers (two blocks per SM) lists
-// fewer; a limit of 0 tests every pair at every step.
+// only those (loaded once per ring half); above, every pair.  The
+// single-instance build for two blocks per SM lists fewer (measured 1-1.5 %
+// faster at K >= 32768 than six); a limit of 0 tests every pair at every step.
 constexpr int kPairListedMax = 6;
 constexpr int kLowRegPairListedMax = 4;
 
@@ -55,26 +55,6 @@ __device__ __forceinline__ bool crash_pair(unsigned long long X, unsigned long l
     return (m0 < 0.0f) | (m1 < 0.0f);
 }
 
-__device__ __forceinline__ float4 lds_v4_each_time(const float4 *a) {
-    float4 r;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
-                 : "r"(static_cast<unsigned>(__cvta_generic_to_shared(a))));
-    return r;
-}
-
-// The crash test against every sphere pair (obs2: sa[j] at 2j, sb[j] at
-// 2j + 1 in shared memory, read at every call: otherwise the loop-invariant
-// loads are hoisted into 128 registers).
-__device__ __forceinline__ bool crash_any(const float4 *obs2, float px, float py, float pz) {
-    const unsigned long long X = pack2(px, px), Y = pack2(py, py), Z = pack2(pz, pz);
-    bool hit = false;
-#pragma unroll
-    for (int j = 0; j < kPairSpheres / 2; ++j)
-        hit |= crash_pair(X, Y, Z, lds_v4_each_time(obs2 + 2 * j), lds_v4_each_time(obs2 + 2 * j + 1));
-    return hit;
-}
-
 // Signed-integer key with the order of the floats (for redux.sync).
 __device__ __forceinline__ int float_order_key(float f) {
     const int b = __float_as_int(f);
@@ -84,28 +64,31 @@ __device__ __forceinline__ float order_key_float(int k) {
     return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff);
 }
 
-// The spheres that some position of this warp's nx states (ring slots xb,
-// 4 kWarp float4 apart) may lie in: the warp's bounding box of the positions,
-// then lane j tests sphere j (s_one: the spheres one by one, shared memory)
+// The spheres that some position of this warp's kPairH states (px, py, pz,
+// in registers) may lie in: the warp's bounding box of the positions, then
+// lane j tests sphere j (s_one: the spheres one by one, shared memory)
 // against the box.  The test is conservative for
-// the FP32 point test of crash_any: a point that test puts inside a sphere is
+// the FP32 point test of crash_pair: a point that test puts inside a sphere is
 // within (1 + 6e-7) r^2 of its centre, and the box distance, computed with a
 // few roundings, is then below 1.001 r^2 + 1e-6.  Padding spheres (-r^2 =
 // 3e38) are never listed; NaN positions are left out of the box (fminf), and
 // their point test is false either way.  Warp-uniform result.
-__device__ __forceinline__ unsigned near_spheres(const float4 *s_one, const float4 *xb, int nx,
-                                                 int lane) {
-    const float inf = __int_as_float(0x7f800000);
-    float lx = inf, ly = inf, lz = inf, hx = -inf, hy = -inf, hz = -inf;
-    for (int s = 0; s < nx; ++s) {
-        const float4 a = xb[s * 4 * kWarp];
-        lx = fminf(lx, a.x);
-        ly = fminf(ly, a.y);
-        lz = fminf(lz, a.z);
-        hx = fmaxf(hx, a.x);
-        hy = fmaxf(hy, a.y);
-        hz = fmaxf(hz, a.z);
+__device__ __forceinline__ unsigned near_spheres(const float4 *s_one, const float *px,
+                                                 const float *py, const float *pz, int lane) {
+    float lx = px[0], ly = py[0], lz = pz[0], hx = px[0], hy = py[0], hz = pz[0];
+#pragma unroll
+    for (int s = 1; s < kPairH; ++s) {
+        lx = fminf(lx, px[s]);
+        ly = fminf(ly, py[s]);
+        lz = fminf(lz, pz[s]);
+        hx = fmaxf(hx, px[s]);
+        hy = fmaxf(hy, py[s]);
+        hz = fmaxf(hz, pz[s]);
     }
+    const float inf = __int_as_float(0x7f800000);
+    if (lx != lx) lx = inf, hx = -inf;  // every position of this lane NaN in x
+    if (ly != ly) ly = inf, hy = -inf;
+    if (lz != lz) lz = inf, hz = -inf;
     const unsigned all = 0xffffffffu;
     lx = order_key_float(__reduce_min_sync(all, float_order_key(lx)));
     ly = order_key_float(__reduce_min_sync(all, float_order_key(ly)));
@@ -346,64 +329,66 @@ __device__ __forceinline__ FloatPair pair_state_cost(const PairArgs &p, const Qu
                                                      int bar_id) {
     const int T = p.T;
     CompSum J;
-    // crash test of every sphere pair (all) or of the n listed pairs (la, lb)
-    auto state = [&](const float4 *slot, int t, bool all, int n, const float4 *la,
-                     const float4 *lb) {
-        const float4 a = slot[0], b = slot[kWarp], d = slot[2 * kWarp], e = slot[3 * kWarp];
-        const float y[13] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, d.x, d.y, d.z, d.w, e.x};
-        const float cs = quad_state_cost(c, y);
-        float r = cs;
-        if (kObstacles) {
-            bool hit = false;
-            if (all) {
-                hit = crash_any(obs2, y[0], y[1], y[2]);
-            } else {
-                const unsigned long long X = pack2(y[0], y[0]), Y = pack2(y[1], y[1]),
-                                         Z = pack2(y[2], y[2]);
-#pragma unroll
-                for (int i = 0; i < kListed; ++i) {
-                    if (i >= n) break;  // warp-uniform
-                    hit |= crash_pair(X, Y, Z, la[i], lb[i]);
-                }
-            }
-            if (hit) r += c.c_crash;
-        }
-        J.add(fmaf(t == T - 1 ? c.s_term : 0.f, cs, r));
-    };
+    // the states of one ring half: first every step's quadratic cost (the
+    // sphere listing's warp reductions run meanwhile), then the crash test of
+    // the sphere pairs near the warp's positions of the half (warp-uniform
+    // list, gathered into registers) or, when more than kListed pairs are
+    // near, of every pair; then the compensated sum in step order
     auto states = [&](int hs) {
         const float4 *xb = ring_x + (hs & 1) * kPairH * 4 * kWarp + lane;
         const int nx = min(kPairH, T - hs * kPairH);
-        // the sphere pairs with a sphere near this warp's positions of the
-        // half (warp-uniform), gathered into registers
-        unsigned pm = 0u;
-        if (kObstacles && kListed > 0) {
-            const unsigned near = near_spheres(s_one, xb, nx, lane);
-            pm = (near | (near >> 1)) & 0x55555555u;  // bit 2j: pair j
-        }
-        const int n = __popc(pm);
-        if (kObstacles && (kListed == 0 || n > kListed)) {
-#pragma unroll 1
-            for (int s = 0; s < nx; ++s)
-                state(xb + s * 4 * kWarp, hs * kPairH + s, true, 0, nullptr, nullptr);
-            return;
-        }
-        float4 la[kListed > 0 ? kListed : 1], lb[kListed > 0 ? kListed : 1];
+        float px[kPairH], py[kPairH], pz[kPairH], cs[kPairH];
 #pragma unroll
-        for (int i = 0; i < kListed; ++i) {
-            if (i >= n) break;
-            const int j = (__ffs(pm) - 1) >> 1;
-            pm &= pm - 1u;
-            la[i] = obs2[2 * j];
-            lb[i] = obs2[2 * j + 1];
+        for (int s = 0; s < kPairH; ++s) {
+            // past nx (the last, partial half) slot nx - 1 again: its position
+            // leaves the box as it is, its cost is not summed
+            const float4 *slot = xb + min(s, nx - 1) * 4 * kWarp;
+            const float4 a = slot[0], b = slot[kWarp], d = slot[2 * kWarp], e = slot[3 * kWarp];
+            const float y[13] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, d.x, d.y, d.z, d.w, e.x};
+            cs[s] = quad_state_cost(c, y);
+            px[s] = a.x;
+            py[s] = a.y;
+            pz[s] = a.z;
         }
-        if (nx == kPairH) {  // straight-line steady state
+        bool hit[kPairH];
 #pragma unroll
-            for (int s = 0; s < kPairH; ++s)
-                state(xb + s * 4 * kWarp, hs * kPairH + s, false, n, la, lb);
-            return;
+        for (int s = 0; s < kPairH; ++s) hit[s] = false;
+        if (kObstacles) {
+            unsigned pm = 0u;
+            if (kListed > 0) {
+                const unsigned near = near_spheres(s_one, px, py, pz, lane);
+                pm = (near | (near >> 1)) & 0x55555555u;  // bit 2j: pair j
+            }
+            const int n = __popc(pm);
+            // one pair's two loads serve the half's kPairH positions
+            auto test_pair = [&](const float4 &la, const float4 &lb) {
+#pragma unroll
+                for (int s = 0; s < kPairH; ++s)
+                    hit[s] |= crash_pair(pack2(px[s], px[s]), pack2(py[s], py[s]),
+                                         pack2(pz[s], pz[s]), la, lb);
+            };
+            if (kListed == 0 || n > kListed) {
+#pragma unroll 4
+                for (int j = 0; j < kPairSpheres / 2; ++j)
+                    test_pair(obs2[2 * j], obs2[2 * j + 1]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < kListed; ++i) {
+                    if (i >= n) break;  // warp-uniform
+                    const int j = (__ffs(pm) - 1) >> 1;
+                    pm &= pm - 1u;
+                    test_pair(obs2[2 * j], obs2[2 * j + 1]);
+                }
+            }
         }
-#pragma unroll 1
-        for (int s = 0; s < nx; ++s) state(xb + s * 4 * kWarp, hs * kPairH + s, false, n, la, lb);
+#pragma unroll
+        for (int s = 0; s < kPairH; ++s) {
+            if (s < nx) {
+                const int t = hs * kPairH + s;
+                const float r = hit[s] ? cs[s] + c.c_crash : cs[s];
+                J.add(fmaf(t == T - 1 ? c.s_term : 0.f, cs[s], r));
+            }
+        }
     };
     group_sync(bar_id, 4 * kWarp);
     for (int hh = 0; hh < nh; ++hh) {

@@ -17,11 +17,14 @@
 //                   sampling terms
 //   cost warp       the quadratic state cost of x_{t+1}, the crash test
 //                   against the (up to 32, padded) spheres, two spheres per
-//                   f32x2 instruction, and the terminal cost; at the end it
-//                   adds the noise warps' partial sums (compensated)
+//                   f32x2 instruction (per ring half only the pairs near the
+//                   warp's positions, when few are), and the terminal cost;
+//                   at the end it adds the noise warps' partial sums
+//                   (compensated)
 //
-// The cost constants (weights, goal, sphere centres and -r^2) are a kernel
-// parameter, so the crash test reads its operands from the constant bank.
+// The cost weights and the goal are a kernel parameter (constant bank); the
+// spheres are staged in shared memory, one by one for the listing and in
+// pairs for the crash test.
 // The warps exchange through a double-buffered ring of kPairH steps per half
 // and meet at one named barrier (bar.sync with the group's id, 128 threads)
 // per half: while the dynamics warp integrates half h, the noise warps write
@@ -45,9 +48,9 @@ namespace {
 // on named barrier 1 + j.  (A block's warp w runs on SM sub-partition
 // w mod 4, so with two groups each sub-partition holds a dynamics and a
 // noise warp, or a noise and a cost warp; pairing each dynamics warp with a
-// cost warp instead measured slower.)  kLowReg: the build for large K, held
-// to 128 registers so that two blocks share an SM.  The spheres are staged
-// in shared memory (one by one, and in pairs).
+// cost warp instead measured slower.)  kLowReg: the build for large K, two
+// blocks per SM, listing at most kLowRegPairListedMax sphere pairs (both
+// builds take under 100 registers).
 template <bool kObstacles, bool kLowReg>
 __global__ void __launch_bounds__(256, kLowReg ? 2 : 1)
     quad_pair_kernel(const StepParams p, const QuadPairConst c) {
@@ -108,9 +111,9 @@ size_t quad_pair_smem_bytes(const mppi_ctx &c, int threads) {
                             8 + kRedFloats + 2 * 4 * kPairSpheres);
 }
 
-// The low-register build (spheres in shared memory, two blocks per SM) once
-// the groups outnumber two per SM; below that the register build keeps the
-// spheres in registers at one block per SM.
+// The build for two blocks per SM once the groups outnumber two per SM;
+// below that the build that lists up to kPairListedMax sphere pairs, one
+// block per SM.
 bool quad_pair_low_reg(const mppi_ctx &c) {
     const long groups = (static_cast<long>(c.K) + kWarp - 1) / kWarp;
     return groups > 2L * c.num_sms;
