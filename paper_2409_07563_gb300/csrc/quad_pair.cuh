@@ -170,57 +170,74 @@ __device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigne
 // RK4 step of the quadrotor (control held over the step), then q <- q / |q|
 // with the reciprocal square root.  The stage combinations run on pairs of
 // state components (f32x2: rounded per element exactly like the scalar
-// fmaf), the derivative on scalars.
+// fmaf), the derivative on scalars.  Pairs (x0, x1), (x3, x4), (x2, x5),
+// (x6, x7), (x8, x9), (x10, x11), (x12, 0): the derivative of the position
+// pair (x0, x1) is then the stage's velocity pair (x3, x4) itself.
 __device__ __forceinline__ void quad_rk4(float x[13], const float v[4], const QuadDynRegs &d,
                                          float dt) {
-    constexpr int NP = 7;  // state pairs (x[12], 0)
-    float k[14], tmp[14];
-    unsigned long long X[NP], A[NP], Kp[NP];
+    constexpr int NP = 7;
+    unsigned long long X[NP], A[NP], Kp[NP], Tm[NP];
     const float h = 0.5f * dt, d6 = dt / 6.0f;
     const unsigned long long H2 = pack2(h, h), DT2 = pack2(dt, dt), D62 = pack2(d6, d6);
     const unsigned long long TWO2 = pack2(2.0f, 2.0f);
     const float fm = v[0] * d.inv_m, f2 = 2.0f * fm;
     const float tau[3] = {v[1], v[2], v[3]};
-#pragma unroll
-    for (int i = 0; i < NP; ++i) X[i] = pack2(x[2 * i], 2 * i + 1 < 13 ? x[2 * i + 1] : 0.f);
-    auto stage = [&](const float *in) {
-        quad_deriv_regs(in, fm, f2, tau, d, k);
-        k[13] = 0.f;
-#pragma unroll
-        for (int i = 0; i < NP; ++i) Kp[i] = pack2(k[2 * i], k[2 * i + 1]);
+    X[0] = pack2(x[0], x[1]);
+    X[1] = pack2(x[3], x[4]);
+    X[2] = pack2(x[2], x[5]);
+    X[3] = pack2(x[6], x[7]);
+    X[4] = pack2(x[8], x[9]);
+    X[5] = pack2(x[10], x[11]);
+    X[6] = pack2(x[12], 0.f);
+    // derivative at the stage input S (pairs as X) into Kp
+    auto stage = [&](const unsigned long long *S) {
+        float y[13], pad;
+        unpack2(S[0], y[0], y[1]);
+        unpack2(S[1], y[3], y[4]);
+        unpack2(S[2], y[2], y[5]);
+        unpack2(S[3], y[6], y[7]);
+        unpack2(S[4], y[8], y[9]);
+        unpack2(S[5], y[10], y[11]);
+        unpack2(S[6], y[12], pad);
+        float k[13];
+        quad_deriv_regs(y, fm, f2, tau, d, k);
+        Kp[0] = S[1];  // (x0, x1)' = (x3, x4)
+        Kp[1] = pack2(k[3], k[4]);
+        Kp[2] = pack2(k[2], k[5]);
+        Kp[3] = pack2(k[6], k[7]);
+        Kp[4] = pack2(k[8], k[9]);
+        Kp[5] = pack2(k[10], k[11]);
+        Kp[6] = pack2(k[12], 0.f);
     };
-    auto unpack_tmp = [&](const unsigned long long *T2) {
-#pragma unroll
-        for (int i = 0; i < NP; ++i) unpack2(T2[i], tmp[2 * i], tmp[2 * i + 1]);
-    };
-    unsigned long long Tm[NP];
-    stage(x);
+    stage(X);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         A[i] = Kp[i];
         Tm[i] = fma2(H2, Kp[i], X[i]);
     }
-    unpack_tmp(Tm);
-    stage(tmp);
+    stage(Tm);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         A[i] = fma2(TWO2, Kp[i], A[i]);
         Tm[i] = fma2(H2, Kp[i], X[i]);
     }
-    unpack_tmp(Tm);
-    stage(tmp);
+    stage(Tm);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         A[i] = fma2(TWO2, Kp[i], A[i]);
         Tm[i] = fma2(DT2, Kp[i], X[i]);
     }
-    unpack_tmp(Tm);
-    stage(tmp);
+    stage(Tm);
 #pragma unroll
     for (int i = 0; i < NP; ++i) X[i] = fma2(D62, add2(A[i], Kp[i]), X[i]);
     float pad;
-#pragma unroll
-    for (int i = 0; i < NP; ++i) unpack2(X[i], x[2 * i], i < NP - 1 ? x[2 * i + 1] : pad);
+    unpack2(X[0], x[0], x[1]);
+    unpack2(X[1], x[3], x[4]);
+    unpack2(X[2], x[2], x[5]);
+    unpack2(X[3], x[6], x[7]);
+    unpack2(X[4], x[8], x[9]);
+    unpack2(X[5], x[10], x[11]);
+    unpack2(X[6], x[12], pad);
     const float inv = rsqrtf((x[6] * x[6] + x[7] * x[7]) + (x[8] * x[8] + x[9] * x[9]));
 #pragma unroll
     for (int i = 6; i < 10; ++i) x[i] *= inv;
